@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""Chebyshev steps/s of the KPM dipole recursion at 16 orbitals / 16 electrons.
+
+Workload (default ``fci16o16e``): seeded synthetic integrals for 16 spatial
+orbitals with 8 alpha + 8 beta electrons (FCI dimension 165,636,900), 32
+Cholesky vectors, z dipole component, 2048 moments.  One Chebyshev step is one
+H~ application, the recursion update and two FP64 dot products on one column
+(Methods, KPM recursion + doubling identities).  A bench step is ``--chunk``
+consecutive Chebyshev steps of one continuing recursion; ``value`` is
+Chebyshev steps per second over the timed steps (all ranks).
+
+Inputs live in HBM before timing starts; every vector (0.66 GB FP32 at 16o) is
+larger than the 129 MB L2, so no flush is needed between steps.
+
+``--impl reference`` times the CPU FP64 oracle (determinant-pair Slater-Condon
+row-pull, all host cores) on a bounded sample of rows of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synthetic  # noqa: E402
+
+METRIC = "Chebyshev steps/s at 16o/16e"
+UNIT = "steps/s"
+
+# DRAM bytes per H application measured by ncu for the dominant kernel, per
+# launch; None until a capture of the current kernel exists.
+NCU_TRAFFIC_BYTES = {}
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=None)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="fci16o16e")
+    p.add_argument("--precision", choices=["fp64", "fp32", "mixed"], default="fp32")
+    p.add_argument("--chunk", type=int, default=None, help="Chebyshev steps per bench step")
+    p.add_argument("--lanczos", type=int, default=24, help="Lanczos steps for a, b (untimed)")
+    p.add_argument("--e2e-requests", type=int, default=2)
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------- distributed
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return ws, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(x: float, pg) -> float:
+    if pg is None:
+        return x
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, pg) -> float:
+    if pg is None:
+        return x
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+# ---------------------------------------------------------------- peaks
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x max SM clock.
+# FP64 peak: the 1.25 TFLOP/s GB300 FP64 rate.
+def alu_peak_tflops(precision: str, sm_max_mhz: float) -> float:
+    if precision == "fp64":
+        return 1.25
+    return 152 * 128 * 2 * sm_max_mhz * 1e6 / 1e12
+
+
+def step_flops(w, nexc, nnbr):
+    """Algorithmic flops of one H application per column: opposite-spin
+    2 n_exc^2 dim (one FMA per alpha-excitation x beta-excitation pair) and
+    same-spin 2 * 2 * nbr2 dim (one FMA per same-spin neighbour, both spins)."""
+    return (2.0 * nexc * nexc + 4.0 * nnbr) * w["dim"]
+
+
+def same_spin_neighbours(n, m):
+    return 1 + m * (n - m) + math.comb(m, 2) * math.comb(n - m, 2)
+
+
+# ---------------------------------------------------------------- CPU oracle baseline
+
+_ORACLE_CACHE = {}
+
+
+def oracle_rate(w, seconds: float, seed: int = 4):
+    """Chebyshev steps/s of the CPU oracle, extrapolated from a timed sample of
+    Slater-Condon row-pull rows plus the FP64 update of the same rows."""
+    import oracle
+    key = (w["norb"], w["nalpha"], w["nbeta"], w["seed"])
+    if key not in _ORACLE_CACHE:
+        I = synthetic.integrals(w["norb"], w["nalpha"], w["nbeta"], w["seed"])
+        sc = oracle.SlaterCondon(I.h1, I.eri, w["norb"], w["nalpha"], w["nbeta"])
+        x = np.random.default_rng(seed).standard_normal(sc.dim)
+        _ORACLE_CACHE[key] = (sc, x)
+    sc, x = _ORACLE_CACHE[key]
+    rng = np.random.default_rng(seed + 1)
+    rows = rng.choice(sc.dim, 2000, replace=False)
+    t0 = time.perf_counter()
+    sc.sigma_rows(rows, x)
+    per_row = (time.perf_counter() - t0) / len(rows)
+    R = int(max(2000, min(sc.dim, seconds / max(per_row, 1e-9))))
+    rows = rng.choice(sc.dim, R, replace=False) if R < sc.dim else np.arange(sc.dim)
+    prev = rng.standard_normal(R)
+    t0 = time.perf_counter()
+    y = sc.sigma_rows(rows, x)
+    nxt = 2.0 * (y - 0.1 * x[rows]) / 3.0 - prev
+    float(x[rows] @ x[rows]), float(nxt @ x[rows])
+    dt = time.perf_counter() - t0
+    t_step = dt * sc.dim / R
+    return 1.0 / t_step, {"kind": "oracle", "cores": oracle.hamiltonian.omp_threads(),
+                          "sample": f"{R} of {sc.dim} determinant rows of one H application "
+                                    f"(FP64 Slater-Condon row-pull) plus their update and dots, "
+                                    f"{dt:.1f} s, extrapolated to a full Chebyshev step"}
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args, ws, rank, local, pg):
+    import torch
+
+    from paper_2506_07430_gb300 import KPM, launch_count
+
+    torch.cuda.set_device(local)
+    w = synthetic.workload(args.workload)
+    n, na, nb = w["norb"], w["nalpha"], w["nbeta"]
+    chunk = args.chunk or {"fp64": 1, "fp32": 1, "mixed": 16}[args.precision]
+    steps = args.steps or {"fp64": 4, "fp32": 8, "mixed": 8}[args.precision]
+    warm = max(3, args.warmup)
+    I = synthetic.integrals(n, na, nb, w["seed"])
+    k = KPM(I.h1, I.eri, I.dipole, n, na, nb, precision=args.precision)
+    dim = k.dim
+    # Ground-state stand-in: a seeded normalised FP64 vector (per rank).
+    psi0_host = synthetic.random_state(dim, 2506000 + rank)
+    psi0 = torch.from_numpy(psi0_host).cuda()
+    emin, emax = k.bounds(iters=args.lanczos, seed=2506001)
+    a, b = KPM.scale(emin, emax)
+    comp = 0b100
+    total_steps = chunk * (warm + steps) + 1
+    k.recursion_begin(psi0, comp, a, b, 2 * total_steps)
+    for _ in range(warm):
+        k.recursion_advance(chunk)
+    torch.cuda.synchronize()
+    barrier(pg)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.4)
+    l0 = launch_count()
+    k.profile_enable(True)
+    k.profile_read()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        k.recursion_advance(chunk)
+    e1.record()
+    torch.cuda.synchronize()
+    launches = launch_count() - l0
+    ms = e0.elapsed_time(e1)
+    sig_ms, sig_cnt = k.profile_read()
+    k.profile_enable(False)
+    clk = clocks.stop()
+    barrier(pg)
+    torch.cuda.synchronize()
+    ms_max = max_over_ranks(ms, pg)
+    steps_all = sum_over_ranks(float(chunk * steps), pg)
+    value = steps_all / (ms_max / 1e3)
+    mom = k.recursion_moments()
+    moments_ok = bool(np.all(np.abs(mom) <= mom[:, :1] * (1 + 1e-6)))
+
+    # roofline of the dominant kernel (the H application)
+    peaks, peak_src = measured_peaks()
+    nexc = na * (n - na + 1)
+    nnbr = same_spin_neighbours(n, na)
+    flops = step_flops(w, nexc, nnbr)
+    per_launch_s = (sig_ms / max(sig_cnt, 1)) / 1e3
+    achieved = flops / per_launch_s / 1e12
+    if args.precision == "mixed":
+        bound, peak = "tensor", float(peaks.get("bf16_tflops_sustained", 1735.0))
+        peak_note = f"bf16 dense sustained, {peak_src}"
+    else:
+        bound = "alu"
+        peak = alu_peak_tflops(args.precision, float(peaks.get("sm_max_mhz", 2070.0)))
+        peak_note = ("FP32 CUDA cores 152 SM x 128 lanes x 2 x max clock" if args.precision == "fp32"
+                     else "GB300 FP64 1.25 TFLOP/s")
+    roof = {"bound": bound, "achieved": round(achieved, 4), "peak": round(peak, 2),
+            "unit": "TFLOP/s", "frac": round(achieved / peak, 6),
+            "traffic": NCU_TRAFFIC_BYTES.get((args.workload, args.precision)),
+            "kernel": "H application (sigma)", "peak_source": peak_note,
+            "algorithmic_flops_per_launch": flops,
+            "launch_ms": round(per_launch_s * 1e3, 4), "launch_share": round(sig_ms / ms, 4),
+            "hbm_floor_ms": round(12.0 * dim / (float(peaks.get("hbm_gbs", 6776.6)) * 1e9) * 1e3, 4)}
+
+    # end to end through the C-ABI with host buffers: psi0 from pinned host memory
+    # H2D, dipole, recursion, moments D2H, per request
+    pinned = torch.empty(dim, dtype=torch.float64, pin_memory=True)
+    pinned.copy_(torch.from_numpy(psi0_host))
+    pin_np = pinned.numpy()
+    nm_e2e = 2 * chunk * 2
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_requests):
+        k.moments(pin_np, comp, a, b, nm_e2e, check_bounds=False)
+    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(e2e_s, pg)
+    e2e_val = sum_over_ranks(args.e2e_requests * nm_e2e / 2, pg) / e2e_s
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, meta = oracle_rate(w, args.cpu_seconds)
+        cpu = dict(value=v, unit=UNIT, **meta)
+
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": steps,
+        "warmup": warm, "ms_per_step": round(ms_max / steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "bf16x3-f32acc"}[args.precision],
+        "data": "synthetic (seeded integrals, seeded normalised state in place of the NQS ground state)",
+        "config": {"workload": args.workload, "norb": n, "nalpha": na, "nbeta": nb, "dim": dim,
+                   "nmoments": w["nmoments"], "chebyshev_steps_per_bench_step": chunk,
+                   "ncol": 1, "precision": args.precision, "parallelism": f"replicas{ws}",
+                   "l2": "inputs larger than L2 (3 vectors of %.2f GB)" % (dim * k.vdtype.itemsize / 1e9),
+                   "a": a, "b": b},
+        "roofline": roof,
+        "e2e": {"value": round(e2e_val, 4), "unit": UNIT, "h2d_bytes_per_step": dim * 8,
+                "d2h_bytes_per_step": nm_e2e * 8,
+                "note": f"kpm_moments_host, {nm_e2e} moments per request, psi0 from pinned host memory"},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "moments_ok": moments_ok,
+    }
+    if cpu is not None:
+        out["cpu_baseline"] = cpu
+    k.close()
+    return out
+
+
+# ---------------------------------------------------------------- reference arm (the oracle)
+
+def run_reference(args, ws, rank, pg):
+    if rank != 0:
+        return None
+    w = synthetic.workload(args.workload)
+    steps = args.steps or 3
+    warm = max(3, args.warmup)
+    per = max(2.0, min(20.0, 150.0 / (steps + warm)))
+    for _ in range(warm):
+        oracle_rate(w, per / 4)
+    rates = []
+    meta = None
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        r, meta = oracle_rate(w, per)
+        rates.append(r)
+    wall = time.perf_counter() - t0
+    value = 1.0 / statistics.mean(1.0 / r for r in rates)
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": steps,
+        "warmup": warm, "ms_per_step": wall / steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "norb": w["norb"], "nalpha": w["nalpha"],
+                   "nbeta": w["nbeta"], "dim": w["dim"], "precision": "fp64"},
+        "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": meta["kind"],
+                         "cores": meta["cores"], "sample": meta["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        # rank 0 alone times the oracle; other ranks exit without work
+        ws = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
+        out = run_reference(args, ws, rank, None)
+        if rank == 0 and out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    ws, rank, local, pg = dist_init()
+    out = run_ours(args, ws, rank, local, pg)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

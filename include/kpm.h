@@ -1,0 +1,219 @@
+/*
+ * kpm.h -- C-ABI of the GB300 (sm_103a) kernel-polynomial-method library.
+ *
+ * The library computes the dipole absorption spectrum of a molecule from its
+ * ground state with the kernel polynomial method of arXiv 2506.07430:
+ *
+ *   I(w) = sum_n |<n|mu|0>|^2 delta(w_n - w)                        (Eq. 1)
+ *   Omega_n = <0| mu T_n(H~) mu |0>,  H~ = (H - b)/a                (Eq. moments)
+ *   alpha_0 = mu|0>, alpha_1 = H~ alpha_0,
+ *   alpha_{n+1} = 2 H~ alpha_n - alpha_{n-1}          (Methods, KPM recursion)
+ *   Omega_2n = 2<alpha_n|alpha_n> - Omega_0,
+ *   Omega_2n+1 = 2<alpha_n+1|alpha_n> - Omega_1       (Methods, doubling)
+ *   I(x) = (g_0 Omega_0 + 2 sum_n g_n Omega_n T_n(x)) / (pi sqrt(1-x^2))
+ *                                          (Eq. kpm with the Jackson kernel g_n)
+ *
+ * H is the second-quantized electronic Hamiltonian of the paper's Methods
+ * ("Mapping fermionic Hamiltonians to the qubits") with one-body integrals h_pq
+ * and two-body integrals, here in chemist order (pq|rs):
+ *   H = sum_pq h_pq E_pq + 1/2 sum_pqrs (pq|rs) (E_pq E_rs - delta_qr E_ps),
+ * E_pq = sum_sigma a+_{p sigma} a_{q sigma}; mu = -sum_pq d_pq E_pq (the paper's
+ * dipole operator without frozen core).  H acts matrix-free on the full
+ * configuration-interaction space of a fixed (N_alpha, N_beta) sector.
+ *
+ * Vector layout (every device vector): determinant (I_alpha, I_beta) is element
+ * I_alpha * N_beta + I_beta (int64), where I is the rank of an occupation string
+ * (an n-bit mask with bit p = orbital p occupied) in ascending integer order.
+ * Block vectors hold ncol columns one after the other: [ncol][dim].
+ * The state of a determinant is (alpha creators ascending)(beta creators
+ * ascending)|vac>.
+ *
+ * Conventions for every call:
+ *  - Host arrays are read during the call and copied; the caller keeps them.
+ *  - Device pointers are owned by the caller, must stay valid until the work
+ *    queued on the context's stream has finished, and must not alias each other
+ *    unless stated.  Device vectors are double* for KPM_FP64 contexts and float*
+ *    otherwise ("void*" below).
+ *  - Calls on one context are not thread-safe; distinct contexts are independent.
+ *  - Errors are returned as kpm_status; no C++ exception crosses the boundary.
+ *    kpm_last_error(ctx) returns the message of the last failing call on ctx
+ *    (kpm_last_error(NULL): last failure of a call without a context, or of
+ *    kpm_create, on this thread).
+ *  - All arithmetic of the path runs in CUDA kernels of this library; there is
+ *    no CPU fallback.  A missing or unusable GPU is reported as KPM_ECUDA.
+ */
+#ifndef KPM_H
+#define KPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kpm_ctx kpm_ctx;
+
+typedef enum {
+    KPM_OK = 0,
+    KPM_EINVAL = 1,      /* invalid argument (size, symmetry, range, null pointer) */
+    KPM_ENOMEM = 2,      /* device or host allocation failed */
+    KPM_ECUDA = 3,       /* CUDA runtime or launch error */
+    KPM_EBOUNDS = 4,     /* |Omega_n| > Omega_0 (1 + 1e-6): [b-a, b+a] misses the spectrum */
+    KPM_ETIMEOUT = 5,    /* a bounded wait ran out */
+    KPM_ECANCELLED = 6,  /* request cancelled */
+    KPM_EUNSUPPORTED = 7 /* valid request outside this build's limits */
+} kpm_status;
+
+typedef enum {
+    KPM_FP64 = 0,   /* FP64 vectors and arithmetic everywhere (reference path)      */
+    KPM_FP32 = 1,   /* FP32 vectors and FP32 CUDA-core sigma; FP64 dots/moments      */
+    KPM_MIXED = 2   /* FP32 vectors; two-electron sigma on tensor cores (tcgen05,
+                       split-BF16 operands, FP32 accumulation); FP64 dots/moments   */
+} kpm_precision;
+
+/* Largest orbital count this build supports (strings are 32-bit masks, string
+ * ranks are 16-bit in packed tables: C(18,9) = 48620 < 65536). */
+#define KPM_MAX_ORB 18
+
+/*
+ * kpm_create -- build a context for one molecule.
+ *   h1     [norb*norb]       host, row-major one-body integrals h_pq, symmetric.
+ *   eri    [norb^4]          host, chemist (pq|rs) at ((p*n+q)*n+r)*n+s,
+ *                            8-fold symmetric.
+ *   dipole [3*norb*norb]     host, d^x, d^y, d^z (Methods, d_pq = <p|r|q>),
+ *                            each symmetric.
+ *   norb   1..KPM_MAX_ORB; 0 <= nalpha, nbeta <= norb.
+ *   prec   kpm_precision of every vector this context reads or writes.
+ *   cuda_stream  cudaStream_t (NULL = legacy default stream) all work is queued on.
+ * Builds the string tables on the device (kernels), uploads the integrals, and
+ * allocates the context's own workspaces.  Symmetry is checked to 1e-12
+ * (relative to max |entry|) -> KPM_EINVAL.  On success *out owns everything it
+ * allocated; release with kpm_destroy.
+ * Paper: Methods, "Mapping fermionic Hamiltonians to the qubits" (H) and
+ * "KPM for absorption spectra" (mu, d_pq).
+ */
+kpm_status kpm_create(const double* h1, const double* eri, const double* dipole,
+                      int norb, int nalpha, int nbeta, kpm_precision prec,
+                      void* cuda_stream, kpm_ctx** out);
+
+/* Releases everything the context allocated (synchronises its stream first). */
+void kpm_destroy(kpm_ctx* ctx);
+
+/* Message of the last failing call (see conventions).  Never NULL. */
+const char* kpm_last_error(const kpm_ctx* ctx);
+
+/* FCI dimension N_alpha_strings * N_beta_strings; -1 for a NULL context. */
+int64_t kpm_dim(const kpm_ctx* ctx);
+
+/* Number of strings, and of single-excitation table entries per string
+ * (m (n - m + 1)), of spin 0 (alpha) or 1 (beta); -1 on bad arguments. */
+int64_t kpm_nstrings(const kpm_ctx* ctx, int spin);
+int kpm_nexc(const kpm_ctx* ctx, int spin);
+
+/*
+ * kpm_string_table -- host copies of the device-built tables of one spin.
+ *   masks [N_s]          occupation masks in rank order.
+ *   tgt   [N_s][n_exc]   rank of the target string J of a+_p a_q |I> = sgn |J>.
+ *   pq    [N_s][n_exc]   p * norb + q.
+ *   sgn   [N_s][n_exc]   +1 / -1.
+ * Entry order per string I: q over occupied orbitals ascending, then p over
+ * {q} union (vacant orbitals) ascending.  Any output pointer may be NULL.
+ * Synchronises the context's stream.
+ */
+kpm_status kpm_string_table(const kpm_ctx* ctx, int spin, uint32_t* masks, int32_t* tgt,
+                            uint16_t* pq, int8_t* sgn);
+
+/*
+ * kpm_sigma -- y = H x for ncol columns (device, [ncol][dim], x and y distinct).
+ * Queued on the context's stream (asynchronous).  FP64: plain gathers in FP64;
+ * FP32: FP32 gathers; MIXED: tensor-core two-electron terms (split-BF16 operands,
+ * FP32 accumulation) plus FP32 gathers.
+ * Paper: Methods, second-quantized Hamiltonian.
+ */
+kpm_status kpm_sigma(kpm_ctx* ctx, const void* x, void* y, int ncol);
+
+/*
+ * kpm_apply_dipole -- y = mu^comp psi (comp 0,1,2 = x,y,z); psi FP64 device
+ * [dim], y device [dim] in the context precision.  Asynchronous.
+ * Paper: Methods, dipole operator mu = -sum_pq d_pq (c+_up c_up + c+_dn c_dn).
+ */
+kpm_status kpm_apply_dipole(kpm_ctx* ctx, int comp, const double* psi_dev, void* y);
+
+/*
+ * kpm_bounds -- spectral bounds of H by `iters` Lanczos steps (FP64 dots and
+ * tridiagonal, vectors in the context precision) from a start vector drawn with
+ * the SplitMix64 counter generator seeded by `seed`.  The extreme Ritz values
+ * are widened by their residual estimates |beta_k s_k|.  Synchronous.
+ * The paper rescales the spectrum into [-1, 1] (Results, "Resolution of
+ * absorption spectra"); pass these bounds to kpm_scale to get a, b.
+ */
+kpm_status kpm_bounds(kpm_ctx* ctx, int iters, uint64_t seed, double* emin, double* emax);
+
+/* a = (emax - emin) / (2 - eps), b = (emax + emin) / 2. */
+void kpm_scale(double emin, double emax, double eps, double* a, double* b);
+
+/*
+ * kpm_moments -- Omega_0 .. Omega_{N-1} for each dipole component set in
+ * comp_mask (bit c = component c), nmoments even and >= 2.
+ *   psi0_dev   FP64 device [dim], the ground state |0> (need not be normalised).
+ *   moments_host  host [popcount(comp_mask)][nmoments], FP64, components in
+ *                 ascending order.
+ * The selected components run as one block vector.  Synchronous.  Returns
+ * KPM_EBOUNDS if some |Omega_n| > Omega_0 (1 + 1e-6) (moments still written).
+ * Paper: Eq. moments; Methods recursion and doubling identities.
+ */
+kpm_status kpm_moments(kpm_ctx* ctx, const double* psi0_dev, unsigned comp_mask, double a,
+                       double b, int nmoments, double* moments_host);
+
+/* As kpm_moments with psi0 in host memory (copied to the device inside). */
+kpm_status kpm_moments_host(kpm_ctx* ctx, const double* psi0_host, unsigned comp_mask,
+                            double a, double b, int nmoments, double* moments_host);
+
+/*
+ * Resumable recursion (the same computation as kpm_moments, in pieces):
+ *   kpm_recursion_begin  alpha_0 = mu psi0, first step; state kept on device.
+ *   kpm_recursion_advance  `nsteps` further Chebyshev steps (asynchronous).
+ *   kpm_recursion_moments  the moments so far into host memory (synchronous);
+ *                          *nmoments_out = 2 * (steps done).
+ * One Chebyshev step = one H~ product, the update and two FP64 dots per column.
+ */
+kpm_status kpm_recursion_begin(kpm_ctx* ctx, const double* psi0_dev, unsigned comp_mask,
+                               double a, double b, int max_moments);
+kpm_status kpm_recursion_advance(kpm_ctx* ctx, int nsteps);
+kpm_status kpm_recursion_moments(kpm_ctx* ctx, double* moments_host, int* nmoments_out);
+
+/*
+ * kpm_spectrum -- Jackson-damped (kernel=1) or undamped (kernel=0) Chebyshev
+ * reconstruction on the npoints Chebyshev nodes x_k = cos(pi (k+1/2)/M):
+ *   I(x) = (g_0 Omega_0 + 2 sum_{n>=1} g_n Omega_n T_n(x)) / (pi sqrt(1-x^2)),
+ *   omega = a x + b, intensity = I(x) / a (density per unit energy),
+ * written in ascending omega.  g_n = [(N-n+1) cos(pi n/(N+1)) +
+ * sin(pi n/(N+1)) cot(pi/(N+1))]/(N+1), n = 0..N-1.  moments, omega_out,
+ * intensity_out are host arrays; the sums run in a CUDA kernel on the current
+ * device's legacy stream.  Synchronous.  No context needed.
+ * Paper: Eq. kpm, Eq. jackson (with the (N-n+1) factor of the KPM review the
+ * paper cites; the printed (N-n-1) gives g_0 != 1).
+ */
+kpm_status kpm_spectrum(const double* moments, int nmoments, double a, double b,
+                        int npoints, int kernel, double* omega_out, double* intensity_out);
+
+/*
+ * Per-launch timing of the H application inside the recursion.
+ * kpm_profile_enable(ctx, 1): every H application queued by later
+ * kpm_recursion_advance calls on ctx is bracketed by a CUDA event pair recorded
+ * on the context's stream.  kpm_profile_read synchronises the stream and
+ * returns the summed device time (ms) and the number of H applications since
+ * the previous read, then resets both.  Disabled by default.
+ */
+kpm_status kpm_profile_enable(kpm_ctx* ctx, int enable);
+kpm_status kpm_profile_read(kpm_ctx* ctx, double* sigma_ms, int* count);
+
+/* Number of kernels this library launched on the calling process so far. */
+uint64_t kpm_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KPM_H */

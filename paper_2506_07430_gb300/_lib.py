@@ -1,0 +1,242 @@
+"""ctypes declarations of include/kpm.h and a small object wrapper."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(_HERE, "_build", "libkpm.so")
+_LIB = None
+
+KPM_OK, KPM_EINVAL, KPM_ENOMEM, KPM_ECUDA, KPM_EBOUNDS, KPM_ETIMEOUT, KPM_ECANCELLED, \
+    KPM_EUNSUPPORTED = range(8)
+_STATUS = {0: "KPM_OK", 1: "KPM_EINVAL", 2: "KPM_ENOMEM", 3: "KPM_ECUDA", 4: "KPM_EBOUNDS",
+           5: "KPM_ETIMEOUT", 6: "KPM_ECANCELLED", 7: "KPM_EUNSUPPORTED"}
+PRECISIONS = {"fp64": 0, "fp32": 1, "mixed": 2}
+
+# Every function declared in include/kpm.h with (restype, argtypes).
+_P, _I, _I64, _U, _U64, _D = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint,
+                              ctypes.c_uint64, ctypes.c_double)
+SIGNATURES = {
+    "kpm_create": (_I, [_P, _P, _P, _I, _I, _I, _I, _P, _P]),
+    "kpm_destroy": (None, [_P]),
+    "kpm_last_error": (ctypes.c_char_p, [_P]),
+    "kpm_dim": (_I64, [_P]),
+    "kpm_nstrings": (_I64, [_P, _I]),
+    "kpm_nexc": (_I, [_P, _I]),
+    "kpm_string_table": (_I, [_P, _I, _P, _P, _P, _P]),
+    "kpm_sigma": (_I, [_P, _P, _P, _I]),
+    "kpm_apply_dipole": (_I, [_P, _I, _P, _P]),
+    "kpm_bounds": (_I, [_P, _I, _U64, _P, _P]),
+    "kpm_scale": (None, [_D, _D, _D, _P, _P]),
+    "kpm_moments": (_I, [_P, _P, _U, _D, _D, _I, _P]),
+    "kpm_moments_host": (_I, [_P, _P, _U, _D, _D, _I, _P]),
+    "kpm_recursion_begin": (_I, [_P, _P, _U, _D, _D, _I]),
+    "kpm_recursion_advance": (_I, [_P, _I]),
+    "kpm_recursion_moments": (_I, [_P, _P, _P]),
+    "kpm_spectrum": (_I, [_P, _I, _D, _D, _I, _I, _P, _P]),
+    "kpm_profile_enable": (_I, [_P, _I]),
+    "kpm_profile_read": (_I, [_P, _P, _P]),
+    "kpm_launch_count": (_U64, []),
+}
+
+
+class KPMError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def library_path() -> str:
+    return _LIBPATH
+
+
+def load_library():
+    """Load libkpm.so (built by ``paper_2506_07430_gb300.build.build()``); raises if absent."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(_LIBPATH):
+            raise RuntimeError(f"{_LIBPATH} is missing: run paper_2506_07430_gb300.build.build() "
+                               "(the CUDA library is required; there is no fallback)")
+        lib = ctypes.CDLL(_LIBPATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = lib
+    return _LIB
+
+
+def launch_count() -> int:
+    return int(load_library().kpm_launch_count())
+
+
+def _check(st: int, ctx=None):
+    if st != KPM_OK:
+        msg = load_library().kpm_last_error(ctx).decode()
+        raise KPMError(st, msg)
+
+
+def _np_ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+def _dev_ptr(t, dtype=None) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA torch.Tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected dtype {dtype}, got {t.dtype}")
+    return t.data_ptr()
+
+
+class KPM:
+    """One molecule: string tables, integrals and workspaces on the GPU."""
+
+    def __init__(self, h1, eri, dipole, norb: int, nalpha: int, nbeta: int,
+                 precision: str = "fp64", stream=None):
+        import torch
+        lib = load_library()
+        self.norb, self.nalpha, self.nbeta = int(norb), int(nalpha), int(nbeta)
+        self.precision = precision
+        n = self.norb
+        h1 = np.ascontiguousarray(h1, dtype=np.float64).reshape(n, n)
+        eri = np.ascontiguousarray(eri, dtype=np.float64).reshape(n, n, n, n)
+        dipole = np.ascontiguousarray(dipole, dtype=np.float64).reshape(3, n, n)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        st = lib.kpm_create(_np_ptr(h1), _np_ptr(eri), _np_ptr(dipole), n, self.nalpha,
+                            self.nbeta, PRECISIONS[precision], ctypes.c_void_p(stream.cuda_stream),
+                            ctypes.byref(h))
+        _check(st, None)
+        self._h = h
+        self.dim = int(lib.kpm_dim(h))
+        self.vdtype = torch.float64 if precision == "fp64" else torch.float32
+
+    # -- helpers
+    def _lib(self):
+        return load_library()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib().kpm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def nstrings(self, spin: int) -> int:
+        return int(self._lib().kpm_nstrings(self._h, spin))
+
+    def nexc(self, spin: int) -> int:
+        return int(self._lib().kpm_nexc(self._h, spin))
+
+    def string_table(self, spin: int):
+        ns, ne = self.nstrings(spin), self.nexc(spin)
+        masks = np.zeros(ns, np.uint32)
+        tgt = np.zeros((ns, ne), np.int32)
+        pq = np.zeros((ns, ne), np.uint16)
+        sgn = np.zeros((ns, ne), np.int8)
+        _check(self._lib().kpm_string_table(self._h, spin, _np_ptr(masks), _np_ptr(tgt),
+                                            _np_ptr(pq), _np_ptr(sgn)), self._h)
+        return masks, tgt, pq, sgn
+
+    def empty(self, ncol: int = 1):
+        import torch
+        return torch.empty((ncol, self.dim), dtype=self.vdtype, device="cuda")
+
+    def sigma(self, x, y=None):
+        """y = H x; x of shape (dim,) or (ncol, dim), dtype float64 (fp64) or float32."""
+        ncol = 1 if x.dim() == 1 else x.shape[0]
+        if y is None:
+            y = x.new_empty(x.shape)
+        _check(self._lib().kpm_sigma(self._h, _dev_ptr(x, self.vdtype), _dev_ptr(y, self.vdtype),
+                                     ncol), self._h)
+        return y
+
+    def apply_dipole(self, comp: int, psi, y=None):
+        import torch
+        if y is None:
+            y = torch.empty(self.dim, dtype=self.vdtype, device="cuda")
+        _check(self._lib().kpm_apply_dipole(self._h, comp, _dev_ptr(psi, torch.float64),
+                                            _dev_ptr(y, self.vdtype)), self._h)
+        return y
+
+    def bounds(self, iters: int = 100, seed: int = 2506000):
+        lo, hi = ctypes.c_double(), ctypes.c_double()
+        _check(self._lib().kpm_bounds(self._h, iters, seed, ctypes.byref(lo), ctypes.byref(hi)),
+               self._h)
+        return lo.value, hi.value
+
+    @staticmethod
+    def scale(emin: float, emax: float, eps: float = 0.01):
+        a, b = ctypes.c_double(), ctypes.c_double()
+        load_library().kpm_scale(emin, emax, eps, ctypes.byref(a), ctypes.byref(b))
+        return a.value, b.value
+
+    def moments(self, psi0, comp_mask: int, a: float, b: float, nmoments: int,
+                check_bounds: bool = True):
+        """Moments [ncomp, nmoments]; psi0 is a CUDA float64 tensor or a host ndarray."""
+        import torch
+        ncomp = bin(comp_mask).count("1")
+        out = np.zeros((ncomp, nmoments), np.float64)
+        if isinstance(psi0, np.ndarray):
+            p = np.ascontiguousarray(psi0, dtype=np.float64)
+            st = self._lib().kpm_moments_host(self._h, _np_ptr(p), comp_mask, a, b, nmoments,
+                                              _np_ptr(out))
+        else:
+            st = self._lib().kpm_moments(self._h, _dev_ptr(psi0, torch.float64), comp_mask, a, b,
+                                         nmoments, _np_ptr(out))
+        if st == KPM_EBOUNDS and not check_bounds:
+            return out
+        _check(st, self._h)
+        return out
+
+    def recursion_begin(self, psi0, comp_mask: int, a: float, b: float, max_moments: int):
+        import torch
+        self._rec_ncomp = bin(comp_mask).count("1")
+        self._rec_max = max_moments
+        _check(self._lib().kpm_recursion_begin(self._h, _dev_ptr(psi0, torch.float64), comp_mask,
+                                               a, b, max_moments), self._h)
+
+    def recursion_advance(self, nsteps: int):
+        _check(self._lib().kpm_recursion_advance(self._h, nsteps), self._h)
+
+    def profile_enable(self, on: bool = True):
+        _check(self._lib().kpm_profile_enable(self._h, 1 if on else 0), self._h)
+
+    def profile_read(self):
+        """(summed ms, count) of H applications since the last read."""
+        ms, cnt = ctypes.c_double(), ctypes.c_int()
+        _check(self._lib().kpm_profile_read(self._h, ctypes.byref(ms), ctypes.byref(cnt)), self._h)
+        return ms.value, cnt.value
+
+    def recursion_moments(self):
+        out = np.zeros((self._rec_ncomp, self._rec_max), np.float64)
+        nm = ctypes.c_int()
+        st = self._lib().kpm_recursion_moments(self._h, _np_ptr(out), ctypes.byref(nm))
+        if st not in (KPM_OK, KPM_EBOUNDS):
+            _check(st, self._h)
+        k = nm.value
+        return out.reshape(-1)[: self._rec_ncomp * k].reshape(self._rec_ncomp, k)
+
+
+def spectrum(moments, a: float, b: float, npoints: int = 2048, kernel: str = "jackson"):
+    """(omega ascending, intensity per unit energy) on the Chebyshev nodes."""
+    lib = load_library()
+    mu = np.ascontiguousarray(moments, dtype=np.float64).reshape(-1)
+    om = np.zeros(npoints, np.float64)
+    it = np.zeros(npoints, np.float64)
+    st = lib.kpm_spectrum(_np_ptr(mu), len(mu), a, b, npoints, 1 if kernel == "jackson" else 0,
+                          _np_ptr(om), _np_ptr(it))
+    _check(st, None)
+    return om, it

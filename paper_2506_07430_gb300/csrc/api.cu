@@ -1,0 +1,504 @@
+// extern "C" entry points of include/kpm.h: context set-up, sigma/dipole
+// dispatch, the KPM recursion driver, Lanczos bounds and the spectrum.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+
+#include "common.cuh"
+#include "sigma_tc.cuh"
+
+using namespace kpm;
+
+static thread_local std::string g_err = "no error";
+
+struct kpm_ctx {
+    int n = 0, na = 0, nb = 0;
+    kpm_precision prec = KPM_FP64;
+    cudaStream_t st = nullptr;
+    int device = 0;
+    int64_t dim = 0;
+    std::string err = "no error";
+
+    DevBuf d_h1, d_eri, d_dip, d_V32;
+    SpinTables ta, tb_own;
+    SpinTables* tb = nullptr;
+    std::unique_ptr<TcSigma> tc;  // tensor-core sigma (KPM_MIXED)
+
+    // recursion state
+    int rec_ncol = 0, rec_steps = 0, rec_max_steps = 0;
+    double rec_a = 1.0, rec_b = 0.0;
+    DevBuf vA, vB, vS, dots, moments_dev, partials, counters, psi_tmp;
+    void* rec_prev = nullptr;
+    void* rec_cur = nullptr;
+
+    // Lanczos state
+    DevBuf lz_v0, lz_v1, lz_w, lz_ab, lz_scalar;
+
+    // profiling of H applications
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;
+    int ev_used = 0;
+
+    ~kpm_ctx() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+
+    size_t esz() const { return prec == KPM_FP64 ? 8 : 4; }
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) KPM_CUDA(cudaSetDevice(dev));
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <class F>
+kpm_status guarded(kpm_ctx* ctx, F&& f) {
+    try {
+        f();
+        return KPM_OK;
+    } catch (const Error& e) {
+        if (ctx) ctx->err = e.msg; else g_err = e.msg;
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        if (ctx) ctx->err = "host allocation failed"; else g_err = "host allocation failed";
+        return KPM_ENOMEM;
+    } catch (...) {
+        if (ctx) ctx->err = "unknown error"; else g_err = "unknown error";
+        return KPM_ECUDA;
+    }
+}
+
+void check_sym(const double* m, int n, const char* what) {
+    double mx = 0.0, d = 0.0;
+    for (int i = 0; i < n * n; ++i) mx = std::fmax(mx, std::fabs(m[i]));
+    for (int p = 0; p < n; ++p)
+        for (int q = 0; q < n; ++q) d = std::fmax(d, std::fabs(m[p * n + q] - m[q * n + p]));
+    if (!(d <= 1e-12 * std::fmax(1.0, mx)))
+        KPM_THROW(KPM_EINVAL, "%s is not symmetric (max asymmetry %.3e)", what, d);
+}
+
+void check_eri(const double* e, int n) {
+    double mx = 0.0, d = 0.0;
+    int64_t n4 = (int64_t)n * n * n * n;
+    for (int64_t i = 0; i < n4; ++i) {
+        if (!std::isfinite(e[i])) KPM_THROW(KPM_EINVAL, "eri has a non-finite entry");
+        mx = std::fmax(mx, std::fabs(e[i]));
+    }
+    auto at = [&](int p, int q, int r, int s) { return e[(((int64_t)p * n + q) * n + r) * n + s]; };
+    for (int p = 0; p < n; ++p)
+        for (int q = 0; q < n; ++q)
+            for (int r = 0; r < n; ++r)
+                for (int s = 0; s < n; ++s) {
+                    double v = at(p, q, r, s);
+                    d = std::fmax(d, std::fabs(v - at(q, p, r, s)));
+                    d = std::fmax(d, std::fabs(v - at(p, q, s, r)));
+                    d = std::fmax(d, std::fabs(v - at(r, s, p, q)));
+                }
+    if (!(d <= 1e-12 * std::fmax(1.0, mx)))
+        KPM_THROW(KPM_EINVAL, "eri lacks 8-fold symmetry (max deviation %.3e)", d);
+}
+
+void require_device() {
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        KPM_THROW(KPM_ECUDA, "no CUDA device available");
+    }
+}
+
+void sigma_dispatch(kpm_ctx* c, const void* x, void* y, int ncol) {
+    if (c->prec == KPM_FP64) {
+        SigmaArgs a{&c->ta, c->tb, c->d_eri.p, c->n, c->dim};
+        sigma_gather_f64(a, (const double*)x, (double*)y, ncol, c->st);
+    } else if (c->prec == KPM_FP32) {
+        SigmaArgs a{&c->ta, c->tb, c->d_V32.p, c->n, c->dim};
+        sigma_gather_f32(a, (const float*)x, (float*)y, ncol, c->st);
+    } else {
+        c->tc->apply((const float*)x, (float*)y, ncol, c->st);
+    }
+}
+
+void dipole_dispatch(kpm_ctx* c, int comp, const double* psi, void* y) {
+    const double* d = c->d_dip.as<double>() + (int64_t)comp * c->n * c->n;
+    if (c->prec == KPM_FP64) dipole_apply_f64(c->ta, *c->tb, d, psi, (double*)y, c->st);
+    else dipole_apply_f32(c->ta, *c->tb, d, psi, (float*)y, c->st);
+}
+
+void update_dispatch(kpm_ctx* c, const void* s, const void* cur, void* prev, int first,
+                     double* dots_at) {
+    int64_t dstride = (int64_t)c->rec_max_steps * 2;
+    if (c->prec == KPM_FP64)
+        cheb_update_f64((const double*)s, (const double*)cur, (double*)prev, c->dim, c->rec_ncol,
+                        c->rec_a, c->rec_b, first, c->partials.as<double>(),
+                        c->counters.as<unsigned>(), dots_at, dstride, c->st);
+    else
+        cheb_update_f32((const float*)s, (const float*)cur, (float*)prev, c->dim, c->rec_ncol,
+                        c->rec_a, c->rec_b, first, c->partials.as<double>(),
+                        c->counters.as<unsigned>(), dots_at, dstride, c->st);
+}
+
+void ensure_reduce_scratch(kpm_ctx* c, int ncol) {
+    size_t pb = (size_t)ncol * 1216 * 2 * sizeof(double);
+    if (c->partials.bytes < pb) c->partials.alloc(pb);
+    size_t cb = (size_t)ncol * sizeof(unsigned) + 64;
+    if (c->counters.bytes < cb) {
+        c->counters.alloc(cb);
+        KPM_CUDA(cudaMemsetAsync(c->counters.p, 0, cb, c->st));
+    }
+}
+
+void rec_begin(kpm_ctx* c, const double* psi0, unsigned mask, double a, double b, int max_moments) {
+    if (!psi0) KPM_THROW(KPM_EINVAL, "psi0 is NULL");
+    if ((mask & ~7u) || !mask) KPM_THROW(KPM_EINVAL, "comp_mask must be a non-empty subset of {1,2,4}");
+    if (max_moments < 2 || (max_moments & 1)) KPM_THROW(KPM_EINVAL, "nmoments must be even and >= 2");
+    if (!(a > 0.0) || !std::isfinite(a) || !std::isfinite(b)) KPM_THROW(KPM_EINVAL, "need a > 0 and finite a, b");
+    int ncol = __builtin_popcount(mask);
+    c->rec_ncol = ncol;
+    c->rec_max_steps = max_moments / 2;
+    c->rec_a = a;
+    c->rec_b = b;
+    size_t vb = (size_t)ncol * c->dim * c->esz();
+    c->vA.ensure(vb);
+    c->vB.ensure(vb);
+    c->vS.ensure(vb);
+    size_t db = (size_t)ncol * c->rec_max_steps * 2 * sizeof(double);
+    c->dots.ensure(db);
+    c->moments_dev.ensure(db);
+    ensure_reduce_scratch(c, ncol);
+    int j = 0;
+    for (int comp = 0; comp < 3; ++comp) {
+        if (!((mask >> comp) & 1)) continue;
+        dipole_dispatch(c, comp, psi0, (char*)c->vB.p + (size_t)j * c->dim * c->esz());
+        ++j;
+    }
+    sigma_dispatch(c, c->vB.p, c->vS.p, ncol);
+    update_dispatch(c, c->vS.p, c->vB.p, c->vA.p, 1, c->dots.as<double>());
+    c->rec_prev = c->vB.p;  // alpha_0
+    c->rec_cur = c->vA.p;   // alpha_1
+    c->rec_steps = 1;
+}
+
+void rec_advance(kpm_ctx* c, int nsteps) {
+    if (c->rec_steps <= 0) KPM_THROW(KPM_EINVAL, "no recursion in progress");
+    if (nsteps < 0 || c->rec_steps + nsteps > c->rec_max_steps)
+        KPM_THROW(KPM_EINVAL, "advance past the requested number of moments");
+    for (int k = 0; k < nsteps; ++k) {
+        if (c->prof) {
+            if ((int)c->ev.size() < c->ev_used + 2) {
+                cudaEvent_t e0, e1;
+                KPM_CUDA(cudaEventCreate(&e0));
+                KPM_CUDA(cudaEventCreate(&e1));
+                c->ev.push_back(e0);
+                c->ev.push_back(e1);
+            }
+            KPM_CUDA(cudaEventRecord(c->ev[c->ev_used], c->st));
+            sigma_dispatch(c, c->rec_cur, c->vS.p, c->rec_ncol);
+            KPM_CUDA(cudaEventRecord(c->ev[c->ev_used + 1], c->st));
+            c->ev_used += 2;
+        } else {
+            sigma_dispatch(c, c->rec_cur, c->vS.p, c->rec_ncol);
+        }
+        update_dispatch(c, c->vS.p, c->rec_cur, c->rec_prev, 0,
+                        c->dots.as<double>() + 2 * (int64_t)c->rec_steps);
+        std::swap(c->rec_prev, c->rec_cur);
+        ++c->rec_steps;
+    }
+}
+
+kpm_status rec_collect(kpm_ctx* c, double* out, int nm_stride) {
+    int ns = c->rec_steps;
+    doubling_combine(c->dots.as<double>(), c->rec_ncol, ns, (int64_t)c->rec_max_steps * 2,
+                     c->moments_dev.as<double>(), 2 * c->rec_max_steps, c->st);
+    for (int j = 0; j < c->rec_ncol; ++j)
+        KPM_CUDA(cudaMemcpyAsync(out + (size_t)j * nm_stride,
+                                 c->moments_dev.as<double>() + (size_t)j * 2 * c->rec_max_steps,
+                                 sizeof(double) * 2 * ns, cudaMemcpyDeviceToHost, c->st));
+    KPM_CUDA(cudaStreamSynchronize(c->st));
+    for (int j = 0; j < c->rec_ncol; ++j) {
+        const double* m = out + (size_t)j * nm_stride;
+        double lim = m[0] * (1.0 + 1e-6);
+        for (int i = 0; i < 2 * ns; ++i)
+            if (!std::isfinite(m[i]) || std::fabs(m[i]) > lim) {
+                c->err = "|Omega_n| exceeds Omega_0: [b-a, b+a] does not contain the spectrum";
+                return KPM_EBOUNDS;
+            }
+    }
+    return KPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+kpm_status kpm_create(const double* h1, const double* eri, const double* dipole, int norb,
+                      int nalpha, int nbeta, kpm_precision prec, void* cuda_stream,
+                      kpm_ctx** out) {
+    if (out) *out = nullptr;
+    std::unique_ptr<kpm_ctx> c;
+    kpm_status s = guarded(nullptr, [&] {
+        if (!out || !h1 || !eri || !dipole) KPM_THROW(KPM_EINVAL, "NULL argument");
+        if (norb < 1 || norb > KPM_MAX_ORB)
+            KPM_THROW(KPM_EINVAL, "norb must be in 1..%d", KPM_MAX_ORB);
+        if (nalpha < 0 || nbeta < 0 || nalpha > norb || nbeta > norb)
+            KPM_THROW(KPM_EINVAL, "electron counts must be in 0..norb");
+        if (prec != KPM_FP64 && prec != KPM_FP32 && prec != KPM_MIXED)
+            KPM_THROW(KPM_EINVAL, "unknown precision %d", (int)prec);
+        check_sym(h1, norb, "h1");
+        for (int cc = 0; cc < 3; ++cc) check_sym(dipole + (size_t)cc * norb * norb, norb, "dipole");
+        check_eri(eri, norb);
+        require_device();
+        c.reset(new kpm_ctx());
+        KPM_CUDA(cudaGetDevice(&c->device));
+        c->n = norb;
+        c->na = nalpha;
+        c->nb = nbeta;
+        c->prec = prec;
+        c->st = (cudaStream_t)cuda_stream;
+        int64_t n2 = (int64_t)norb * norb, n4 = n2 * n2;
+        c->d_h1.alloc(n2 * 8);
+        c->d_eri.alloc(n4 * 8);
+        c->d_dip.alloc(3 * n2 * 8);
+        KPM_CUDA(cudaMemcpyAsync(c->d_h1.p, h1, n2 * 8, cudaMemcpyHostToDevice, c->st));
+        KPM_CUDA(cudaMemcpyAsync(c->d_eri.p, eri, n4 * 8, cudaMemcpyHostToDevice, c->st));
+        KPM_CUDA(cudaMemcpyAsync(c->d_dip.p, dipole, 3 * n2 * 8, cudaMemcpyHostToDevice, c->st));
+        build_spin_tables(c->ta, norb, nalpha, c->d_h1.as<double>(), c->d_eri.as<double>(), c->st);
+        if (nbeta == nalpha) {
+            c->tb = &c->ta;
+        } else {
+            build_spin_tables(c->tb_own, norb, nbeta, c->d_h1.as<double>(), c->d_eri.as<double>(),
+                              c->st);
+            c->tb = &c->tb_own;
+        }
+        c->dim = c->ta.ns * c->tb->ns;
+        if (prec == KPM_FP32) {
+            c->d_V32.alloc(n4 * 4);
+            to_f32(c->d_eri.as<double>(), c->d_V32.as<float>(), n4, c->st);
+        }
+        if (prec == KPM_MIXED) {
+            c->tc.reset(new TcSigma());
+            c->tc->init(c->ta, *c->tb, h1, eri, norb, c->st);
+        }
+        KPM_CUDA(cudaStreamSynchronize(c->st));
+    });
+    if (s == KPM_OK) *out = c.release();
+    return s;
+}
+
+void kpm_destroy(kpm_ctx* ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->st);
+    delete ctx;
+}
+
+const char* kpm_last_error(const kpm_ctx* ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
+
+int64_t kpm_dim(const kpm_ctx* ctx) { return ctx ? ctx->dim : -1; }
+
+int64_t kpm_nstrings(const kpm_ctx* ctx, int spin) {
+    if (!ctx || (spin != 0 && spin != 1)) return -1;
+    return spin == 0 ? ctx->ta.ns : ctx->tb->ns;
+}
+
+int kpm_nexc(const kpm_ctx* ctx, int spin) {
+    if (!ctx || (spin != 0 && spin != 1)) return -1;
+    return spin == 0 ? ctx->ta.nexc : ctx->tb->nexc;
+}
+
+kpm_status kpm_string_table(const kpm_ctx* ctx_c, int spin, uint32_t* masks, int32_t* tgt,
+                            uint16_t* pq, int8_t* sgn) {
+    kpm_ctx* ctx = const_cast<kpm_ctx*>(ctx_c);
+    if (!ctx) { g_err = "NULL context"; return KPM_EINVAL; }
+    return guarded(ctx, [&] {
+        if (spin != 0 && spin != 1) KPM_THROW(KPM_EINVAL, "spin must be 0 or 1");
+        DeviceGuard g(ctx->device);
+        const SpinTables& t = spin == 0 ? ctx->ta : *ctx->tb;
+        size_t ne = (size_t)t.ns * t.nexc;
+        KPM_CUDA(cudaStreamSynchronize(ctx->st));
+        if (masks) KPM_CUDA(cudaMemcpy(masks, t.masks.p, t.ns * 4, cudaMemcpyDeviceToHost));
+        if (tgt && ne) KPM_CUDA(cudaMemcpy(tgt, t.tgt.p, ne * 4, cudaMemcpyDeviceToHost));
+        if (pq && ne) KPM_CUDA(cudaMemcpy(pq, t.pq.p, ne * 2, cudaMemcpyDeviceToHost));
+        if (sgn && ne) KPM_CUDA(cudaMemcpy(sgn, t.sgn.p, ne, cudaMemcpyDeviceToHost));
+    });
+}
+
+kpm_status kpm_sigma(kpm_ctx* ctx, const void* x, void* y, int ncol) {
+    if (!ctx) { g_err = "NULL context"; return KPM_EINVAL; }
+    return guarded(ctx, [&] {
+        if (!x || !y || ncol < 1 || ncol > 64) KPM_THROW(KPM_EINVAL, "bad sigma arguments");
+        if (x == y) KPM_THROW(KPM_EINVAL, "x and y must not alias");
+        DeviceGuard g(ctx->device);
+        sigma_dispatch(ctx, x, y, ncol);
+    });
+}
+
+kpm_status kpm_apply_dipole(kpm_ctx* ctx, int comp, const double* psi, void* y) {
+    if (!ctx) { g_err = "NULL context"; return KPM_EINVAL; }
+    return guarded(ctx, [&] {
+        if (comp < 0 || comp > 2 || !psi || !y) KPM_THROW(KPM_EINVAL, "bad dipole arguments");
+        DeviceGuard g(ctx->device);
+        dipole_dispatch(ctx, comp, psi, y);
+    });
+}
+
+void kpm_scale(double emin, double emax, double eps, double* a, double* b) {
+    if (a) *a = (emax - emin) / (2.0 - eps);
+    if (b) *b = 0.5 * (emax + emin);
+}
+
+kpm_status kpm_bounds(kpm_ctx* ctx, int iters, uint64_t seed, double* emin, double* emax) {
+    if (!ctx) { g_err = "NULL context"; return KPM_EINVAL; }
+    return guarded(ctx, [&] {
+        if (iters < 1 || iters > 4096 || !emin || !emax) KPM_THROW(KPM_EINVAL, "bad bounds arguments");
+        DeviceGuard g(ctx->device);
+        int k = (int)std::min<int64_t>(iters, ctx->dim);
+        bool f64 = ctx->prec == KPM_FP64;
+        size_t vb = (size_t)ctx->dim * ctx->esz();
+        ctx->lz_v0.ensure(vb);
+        ctx->lz_v1.ensure(vb);
+        ctx->lz_w.ensure(vb);
+        ctx->lz_ab.ensure(sizeof(double) * 2 * (k + 1));
+        ctx->lz_scalar.ensure(sizeof(double) * 8);
+        ensure_reduce_scratch(ctx, 1);
+        double* al = ctx->lz_ab.as<double>();
+        double* be = al + (k + 1);
+        double* sc = ctx->lz_scalar.as<double>();
+        double* parts = ctx->partials.as<double>();
+        unsigned* cnt = ctx->counters.as<unsigned>();
+        void* v = ctx->lz_v0.p;
+        void* vp = ctx->lz_v1.p;
+        void* w = ctx->lz_w.p;
+        fill_random(v, ctx->dim, f64, seed, ctx->st);
+        dot_dev(v, v, ctx->dim, f64, parts, cnt, sc, ctx->st);
+        scale_inplace(v, ctx->dim, f64, sc, ctx->st);
+        for (int j = 0; j < k; ++j) {
+            sigma_dispatch(ctx, v, w, 1);
+            dot_dev(w, v, ctx->dim, f64, parts, cnt, al + j, ctx->st);
+            lanczos_orth(w, v, j ? vp : nullptr, ctx->dim, f64, al + j, j ? be + j - 1 : nullptr,
+                         parts, cnt, sc, ctx->st);
+            lanczos_scale(vp, w, ctx->dim, f64, sc, be + j, ctx->st);
+            std::swap(v, vp);  // v <- v_{j+1}, vp <- v_j
+        }
+        tridiag_extremes(al, be, k, sc + 2, ctx->st);
+        double out4[4];
+        KPM_CUDA(cudaMemcpyAsync(out4, sc + 2, sizeof(out4), cudaMemcpyDeviceToHost, ctx->st));
+        KPM_CUDA(cudaStreamSynchronize(ctx->st));
+        *emin = out4[0] - out4[2];
+        *emax = out4[1] + out4[3];
+    });
+}
+
+kpm_status kpm_recursion_begin(kpm_ctx* ctx, const double* psi0_dev, unsigned comp_mask, double a,
+                               double b, int max_moments) {
+    if (!ctx) { g_err = "NULL context"; return KPM_EINVAL; }
+    return guarded(ctx, [&] {
+        DeviceGuard g(ctx->device);
+        rec_begin(ctx, psi0_dev, comp_mask, a, b, max_moments);
+    });
+}
+
+kpm_status kpm_recursion_advance(kpm_ctx* ctx, int nsteps) {
+    if (!ctx) { g_err = "NULL context"; return KPM_EINVAL; }
+    return guarded(ctx, [&] {
+        DeviceGuard g(ctx->device);
+        rec_advance(ctx, nsteps);
+    });
+}
+
+kpm_status kpm_recursion_moments(kpm_ctx* ctx, double* out, int* nm_out) {
+    if (!ctx) { g_err = "NULL context"; return KPM_EINVAL; }
+    kpm_status r = KPM_OK;
+    kpm_status s = guarded(ctx, [&] {
+        if (!out) KPM_THROW(KPM_EINVAL, "NULL output");
+        if (ctx->rec_steps <= 0) KPM_THROW(KPM_EINVAL, "no recursion in progress");
+        DeviceGuard g(ctx->device);
+        r = rec_collect(ctx, out, 2 * ctx->rec_steps);
+        if (nm_out) *nm_out = 2 * ctx->rec_steps;
+    });
+    return s != KPM_OK ? s : r;
+}
+
+kpm_status kpm_moments(kpm_ctx* ctx, const double* psi0_dev, unsigned comp_mask, double a,
+                       double b, int nmoments, double* moments_host) {
+    if (!ctx) { g_err = "NULL context"; return KPM_EINVAL; }
+    kpm_status r = KPM_OK;
+    kpm_status s = guarded(ctx, [&] {
+        if (!moments_host) KPM_THROW(KPM_EINVAL, "NULL output");
+        DeviceGuard g(ctx->device);
+        rec_begin(ctx, psi0_dev, comp_mask, a, b, nmoments);
+        rec_advance(ctx, nmoments / 2 - 1);
+        r = rec_collect(ctx, moments_host, nmoments);
+    });
+    return s != KPM_OK ? s : r;
+}
+
+kpm_status kpm_moments_host(kpm_ctx* ctx, const double* psi0_host, unsigned comp_mask, double a,
+                            double b, int nmoments, double* moments_host) {
+    if (!ctx) { g_err = "NULL context"; return KPM_EINVAL; }
+    kpm_status s = guarded(ctx, [&] {
+        if (!psi0_host) KPM_THROW(KPM_EINVAL, "NULL psi0");
+        DeviceGuard g(ctx->device);
+        ctx->psi_tmp.ensure((size_t)ctx->dim * 8);
+        KPM_CUDA(cudaMemcpyAsync(ctx->psi_tmp.p, psi0_host, (size_t)ctx->dim * 8,
+                                 cudaMemcpyHostToDevice, ctx->st));
+    });
+    if (s != KPM_OK) return s;
+    return kpm_moments(ctx, ctx->psi_tmp.as<double>(), comp_mask, a, b, nmoments, moments_host);
+}
+
+kpm_status kpm_spectrum(const double* moments, int nmoments, double a, double b, int npoints,
+                        int kernel, double* omega_out, double* intensity_out) {
+    return guarded(nullptr, [&] {
+        if (!moments || !omega_out || !intensity_out) KPM_THROW(KPM_EINVAL, "NULL argument");
+        if (nmoments < 1 || npoints < 1 || (kernel != 0 && kernel != 1))
+            KPM_THROW(KPM_EINVAL, "bad spectrum arguments");
+        if (!(a > 0.0)) KPM_THROW(KPM_EINVAL, "a must be > 0");
+        require_device();
+        DevBuf dm, dd, dom, din;
+        dm.alloc(sizeof(double) * nmoments);
+        dd.alloc(sizeof(double) * nmoments);
+        dom.alloc(sizeof(double) * npoints);
+        din.alloc(sizeof(double) * npoints);
+        KPM_CUDA(cudaMemcpy(dm.p, moments, sizeof(double) * nmoments, cudaMemcpyHostToDevice));
+        spectrum_dev(dm.as<double>(), nmoments, a, b, npoints, kernel, dd.as<double>(),
+                     dom.as<double>(), din.as<double>(), nullptr);
+        KPM_CUDA(cudaMemcpy(omega_out, dom.p, sizeof(double) * npoints, cudaMemcpyDeviceToHost));
+        KPM_CUDA(cudaMemcpy(intensity_out, din.p, sizeof(double) * npoints, cudaMemcpyDeviceToHost));
+    });
+}
+
+kpm_status kpm_profile_enable(kpm_ctx* ctx, int enable) {
+    if (!ctx) { g_err = "NULL context"; return KPM_EINVAL; }
+    ctx->prof = enable != 0;
+    return KPM_OK;
+}
+
+kpm_status kpm_profile_read(kpm_ctx* ctx, double* ms, int* count) {
+    if (!ctx) { g_err = "NULL context"; return KPM_EINVAL; }
+    return guarded(ctx, [&] {
+        DeviceGuard g(ctx->device);
+        KPM_CUDA(cudaStreamSynchronize(ctx->st));
+        double tot = 0.0;
+        for (int i = 0; i + 1 < ctx->ev_used; i += 2) {
+            float t = 0.f;
+            KPM_CUDA(cudaEventElapsedTime(&t, ctx->ev[i], ctx->ev[i + 1]));
+            tot += t;
+        }
+        if (ms) *ms = tot;
+        if (count) *count = ctx->ev_used / 2;
+        ctx->ev_used = 0;
+    });
+}
+
+uint64_t kpm_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"

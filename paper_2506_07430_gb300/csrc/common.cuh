@@ -1,0 +1,164 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "kpm.h"
+
+namespace kpm {
+
+// ---------------------------------------------------------------- errors
+
+struct Error {
+    kpm_status status;
+    std::string msg;
+};
+
+// Thrown inside the library only; every extern "C" entry point catches it.
+#define KPM_THROW(st, ...)                                                       \
+    do {                                                                         \
+        char _buf[512];                                                          \
+        snprintf(_buf, sizeof(_buf), __VA_ARGS__);                               \
+        throw ::kpm::Error{(st), std::string(_buf)};                             \
+    } while (0)
+
+#define KPM_CUDA(call)                                                           \
+    do {                                                                         \
+        cudaError_t _e = (call);                                                 \
+        if (_e != cudaSuccess)                                                   \
+            KPM_THROW(KPM_ECUDA, "%s:%d %s: %s", __FILE__, __LINE__, #call,      \
+                      cudaGetErrorString(_e));                                   \
+    } while (0)
+
+// Every kernel launch of the library goes through this counter.
+extern std::atomic<uint64_t> g_launches;
+
+#define KPM_LAUNCHED()                                                           \
+    do {                                                                         \
+        ::kpm::g_launches.fetch_add(1, std::memory_order_relaxed);               \
+        cudaError_t _e = cudaGetLastError();                                     \
+        if (_e != cudaSuccess)                                                   \
+            KPM_THROW(KPM_ECUDA, "%s:%d launch: %s", __FILE__, __LINE__,         \
+                      cudaGetErrorString(_e));                                   \
+    } while (0)
+
+// ---------------------------------------------------------------- device buffers
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    void alloc(size_t n) {
+        release();
+        if (n == 0) return;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            cudaGetLastError();
+            KPM_THROW(KPM_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", n, cudaGetErrorString(e));
+        }
+        bytes = n;
+    }
+    void ensure(size_t n) {
+        if (n > bytes) alloc(n);
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// ---------------------------------------------------------------- string tables
+
+// One spin's occupation strings and single-excitation tables, all on the device.
+struct SpinTables {
+    int n = 0, m = 0;        // orbitals, electrons of this spin
+    int64_t ns = 0;          // number of strings C(n, m)
+    int nexc = 0;            // m (n - m + 1)
+    int nnbr = 0;            // same-spin neighbours incl. itself: 1 + m(n-m) + C(m,2) C(n-m,2)
+    DevBuf masks;            // uint32 [ns]
+    DevBuf tgt, pq, sgn;     // int32/uint16/int8 [ns][nexc]  (API layout)
+    DevBuf tgtT, pqT, sgnT;  // int32/uint16/int8 [nexc][ns]  (string-fastest, coalesced)
+    DevBuf fcol;             // int32  [nnbr][ns]  same-spin string Hamiltonian columns
+    DevBuf fval64;           // double [nnbr][ns]
+    DevBuf fval32;           // float  [nnbr][ns]
+};
+
+// Device binomial table C(p, k) for p, k <= KPM_MAX_ORB.
+struct Binom {
+    uint32_t c[KPM_MAX_ORB + 1][KPM_MAX_ORB + 1];
+};
+Binom make_binom();
+
+void build_spin_tables(SpinTables& t, int n, int m, const double* d_h1, const double* d_eri,
+                       cudaStream_t st);
+
+// y[i] = (float) x[i]
+void to_f32(const double* x, float* y, int64_t n, cudaStream_t st);
+
+// ---------------------------------------------------------------- sigma (gather kernels)
+
+struct SigmaArgs {
+    const SpinTables* ta;
+    const SpinTables* tb;
+    const void* V;     // (pq|rs) as [n*n][n*n], double or float by path
+    int n;
+    int64_t dim;
+};
+
+void sigma_gather_f64(const SigmaArgs& a, const double* x, double* y, int ncol, cudaStream_t st);
+void sigma_gather_f32(const SigmaArgs& a, const float* x, float* y, int ncol, cudaStream_t st);
+
+void dipole_apply_f64(const SpinTables& ta, const SpinTables& tb, const double* d_dip,
+                      const double* psi, double* y, cudaStream_t st);
+void dipole_apply_f32(const SpinTables& ta, const SpinTables& tb, const double* d_dip,
+                      const double* psi, float* y, cudaStream_t st);
+
+// ---------------------------------------------------------------- recursion helpers
+
+// Fixed reduction grid for a vector of length dim (deterministic partial order).
+int reduce_blocks(int64_t dim);
+
+// alpha_next = first ? (s - b c)/a : 2 (s - b c)/a - prev, written over prev;
+// dots[col*stride + 0] = <c|c>, dots[col*stride + 1] = <next|c> (FP64).
+void cheb_update_f64(const double* s, const double* c, double* prev, int64_t dim, int ncol,
+                     double a, double b, int first, double* partials, unsigned* counters,
+                     double* dots, int64_t dots_col_stride, cudaStream_t st);
+void cheb_update_f32(const float* s, const float* c, float* prev, int64_t dim, int ncol,
+                     double a, double b, int first, double* partials, unsigned* counters,
+                     double* dots, int64_t dots_col_stride, cudaStream_t st);
+
+// moments[col][2n], [2n+1] from dots[col][n][2] (doubling identities).
+void doubling_combine(const double* dots, int ncol, int nsteps, int64_t dots_col_stride,
+                      double* moments, int nmoments_stride, cudaStream_t st);
+
+// Lanczos pieces (FP64 scalars on the device).
+void dot_dev(const void* x, const void* y, int64_t dim, bool f64, double* partials,
+             unsigned* counters, double* out, cudaStream_t st);
+void lanczos_orth(void* w, const void* v, const void* vprev, int64_t dim, bool f64,
+                  const double* alpha, const double* beta_prev, double* partials,
+                  unsigned* counters, double* norm2_out, cudaStream_t st);
+void lanczos_scale(void* vnext, const void* w, int64_t dim, bool f64, const double* norm2,
+                   double* beta_out, cudaStream_t st);
+void fill_random(void* v, int64_t dim, bool f64, uint64_t seed, cudaStream_t st);
+void scale_inplace(void* v, int64_t dim, bool f64, const double* norm2, cudaStream_t st);
+void tridiag_extremes(const double* alpha, const double* beta, int k, double* out4,
+                      cudaStream_t st);
+
+// Spectrum on the device: moments (device) -> omega, intensity (device);
+// `damped` is device scratch of N doubles (g_n Omega_n with the factor 2 for n >= 1).
+void spectrum_dev(const double* moments, int N, double a, double b, int M, int kernel,
+                  double* damped, double* omega, double* intensity, cudaStream_t st);
+
+}  // namespace kpm

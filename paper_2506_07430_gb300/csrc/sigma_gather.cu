@@ -1,0 +1,150 @@
+// Gather-form sigma = H x and dipole mu x (FP64 and FP32 CUDA-core paths).
+//
+// H (Methods, second-quantized Hamiltonian) splits over the alpha/beta string
+// product basis as
+//   H = F_alpha (x) 1 + 1 (x) F_beta + sum_{pq,rs} (pq|rs) E^alpha_pq E^beta_rs,
+// where F_sigma is the same-spin string Hamiltonian (built in tables.cu) and the
+// last term is the opposite-spin two-electron part.  For determinant
+// (I_a, I_b) and x laid out as x[J_a * N_b + J_b]:
+//   y = sum_t F_b[I_b,t] x[I_a, J_t] + sum_t F_a[I_a,t] x[J_t, I_b]
+//     + sum_{e in tab(I_a)} s_e sum_{f in tab(I_b)} s_f (pq_e|pq_f) x[J_e, J_f]
+// using <I|E_pq|J> = <J|E_qp|I> and (pq|rs) = (qp|sr) for real orbitals.
+//
+// The dipole (Methods, mu = -sum_pq d_pq (E^alpha_pq + E^beta_pq)) is a
+// one-body gather over the same tables.
+//
+// One CTA row handles one alpha string and 128 consecutive beta strings; the
+// alpha-side table row and F_alpha row are staged in shared memory and read
+// uniformly; beta-side rows are read from the string-fastest tables, so
+// neighbouring threads load neighbouring words.
+#include "common.cuh"
+
+namespace kpm {
+
+template <class T>
+__global__ void __launch_bounds__(128)
+k_sigma_gather(const T* __restrict__ x, T* __restrict__ y, int64_t nsa, int64_t nsb,
+               const int32_t* __restrict__ tgtA, const uint16_t* __restrict__ pqA,
+               const int8_t* __restrict__ sgnA, int nexcA, const int32_t* __restrict__ fcolA,
+               const T* __restrict__ fvalA, int nnbrA, const int32_t* __restrict__ tgtBT,
+               const uint16_t* __restrict__ pqBT, const int8_t* __restrict__ sgnBT, int nexcB,
+               const int32_t* __restrict__ fcolB, const T* __restrict__ fvalB, int nnbrB,
+               const T* __restrict__ V, int n2) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    T* sFv = reinterpret_cast<T*>(smem);
+    int32_t* sFc = reinterpret_cast<int32_t*>(sFv + nnbrA);
+    int32_t* sJ = sFc + nnbrA;
+    int32_t* sP = sJ + nexcA;
+    int32_t* sS = sP + nexcA;
+
+    const int64_t ia = blockIdx.y;
+    const int64_t ib = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t dim = nsa * nsb;
+    x += (int64_t)blockIdx.z * dim;
+    y += (int64_t)blockIdx.z * dim;
+
+    for (int t = threadIdx.x; t < nnbrA; t += blockDim.x) {
+        sFv[t] = fvalA[(int64_t)t * nsa + ia];
+        sFc[t] = fcolA[(int64_t)t * nsa + ia];
+    }
+    for (int e = threadIdx.x; e < nexcA; e += blockDim.x) {
+        sJ[e] = tgtA[ia * nexcA + e];
+        sP[e] = pqA[ia * nexcA + e];
+        sS[e] = sgnA[ia * nexcA + e];
+    }
+    __syncthreads();
+    if (ib >= nsb) return;
+
+    const T* xrow = x + ia * nsb;
+    T acc = T(0);
+    // same-spin beta: row I_a of x, columns = F_beta neighbours of I_b
+    for (int t = 0; t < nnbrB; ++t)
+        acc += fvalB[(int64_t)t * nsb + ib] * xrow[fcolB[(int64_t)t * nsb + ib]];
+    // same-spin alpha: column I_b of x, rows = F_alpha neighbours of I_a
+    for (int t = 0; t < nnbrA; ++t) acc += sFv[t] * x[(int64_t)sFc[t] * nsb + ib];
+    // opposite-spin two-electron part
+    for (int f = 0; f < nexcB; ++f) {
+        const int64_t jb = tgtBT[(int64_t)f * nsb + ib];
+        const int pb = pqBT[(int64_t)f * nsb + ib];
+        const T sb = T(sgnBT[(int64_t)f * nsb + ib]);
+        T inner = T(0);
+        for (int e = 0; e < nexcA; ++e)
+            inner += T(sS[e]) * V[(int64_t)sP[e] * n2 + pb] * x[(int64_t)sJ[e] * nsb + jb];
+        acc += sb * inner;
+    }
+    y[ia * nsb + ib] = acc;
+}
+
+template <class T>
+static void launch_sigma(const SigmaArgs& a, const T* x, T* y, int ncol, const T* fvA,
+                         const T* fvB, cudaStream_t st) {
+    const SpinTables& A = *a.ta;
+    const SpinTables& B = *a.tb;
+    if (ncol <= 0 || a.dim == 0) return;
+    dim3 grid((unsigned)((B.ns + 127) / 128), (unsigned)A.ns, (unsigned)ncol);
+    size_t sm = (size_t)A.nnbr * (sizeof(T) + 4) + (size_t)A.nexc * 12 + 16;
+    if (sm > 48 * 1024)
+        KPM_CUDA(cudaFuncSetAttribute(k_sigma_gather<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sm));
+    k_sigma_gather<T><<<grid, 128, sm, st>>>(
+        x, y, A.ns, B.ns, A.tgt.as<int32_t>(), A.pq.as<uint16_t>(), A.sgn.as<int8_t>(), A.nexc,
+        A.fcol.as<int32_t>(), fvA, A.nnbr, B.tgtT.as<int32_t>(), B.pqT.as<uint16_t>(),
+        B.sgnT.as<int8_t>(), B.nexc, B.fcol.as<int32_t>(), fvB, B.nnbr,
+        static_cast<const T*>(a.V), a.n * a.n);
+    KPM_LAUNCHED();
+}
+
+void sigma_gather_f64(const SigmaArgs& a, const double* x, double* y, int ncol, cudaStream_t st) {
+    launch_sigma<double>(a, x, y, ncol, a.ta->fval64.as<double>(), a.tb->fval64.as<double>(), st);
+}
+void sigma_gather_f32(const SigmaArgs& a, const float* x, float* y, int ncol, cudaStream_t st) {
+    launch_sigma<float>(a, x, y, ncol, a.ta->fval32.as<float>(), a.tb->fval32.as<float>(), st);
+}
+
+// ---------------------------------------------------------------- dipole
+
+template <class T>
+__global__ void __launch_bounds__(128)
+k_dipole(const double* __restrict__ psi, T* __restrict__ y, int64_t nsa, int64_t nsb,
+         const int32_t* __restrict__ tgtA, const uint16_t* __restrict__ pqA,
+         const int8_t* __restrict__ sgnA, int nexcA, const int32_t* __restrict__ tgtBT,
+         const uint16_t* __restrict__ pqBT, const int8_t* __restrict__ sgnBT, int nexcB,
+         const double* __restrict__ d) {
+    const int64_t ia = blockIdx.y;
+    const int64_t ib = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ib >= nsb) return;
+    double acc = 0.0;
+    for (int e = 0; e < nexcA; ++e) {
+        int64_t ja = tgtA[ia * nexcA + e];
+        acc += d[pqA[ia * nexcA + e]] * (double)sgnA[ia * nexcA + e] * psi[ja * nsb + ib];
+    }
+    const double* prow = psi + ia * nsb;
+    for (int f = 0; f < nexcB; ++f) {
+        int64_t jb = tgtBT[(int64_t)f * nsb + ib];
+        acc += d[pqBT[(int64_t)f * nsb + ib]] * (double)sgnBT[(int64_t)f * nsb + ib] * prow[jb];
+    }
+    y[ia * nsb + ib] = (T)(-acc);
+}
+
+template <class T>
+static void launch_dipole(const SpinTables& A, const SpinTables& B, const double* d,
+                          const double* psi, T* y, cudaStream_t st) {
+    if (A.ns * B.ns == 0) return;
+    dim3 grid((unsigned)((B.ns + 127) / 128), (unsigned)A.ns);
+    k_dipole<T><<<grid, 128, 0, st>>>(psi, y, A.ns, B.ns, A.tgt.as<int32_t>(),
+                                      A.pq.as<uint16_t>(), A.sgn.as<int8_t>(), A.nexc,
+                                      B.tgtT.as<int32_t>(), B.pqT.as<uint16_t>(),
+                                      B.sgnT.as<int8_t>(), B.nexc, d);
+    KPM_LAUNCHED();
+}
+
+void dipole_apply_f64(const SpinTables& ta, const SpinTables& tb, const double* d,
+                      const double* psi, double* y, cudaStream_t st) {
+    launch_dipole<double>(ta, tb, d, psi, y, st);
+}
+void dipole_apply_f32(const SpinTables& ta, const SpinTables& tb, const double* d,
+                      const double* psi, float* y, cudaStream_t st) {
+    launch_dipole<float>(ta, tb, d, psi, y, st);
+}
+
+}  // namespace kpm
