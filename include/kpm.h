@@ -199,6 +199,14 @@ kpm_status kpm_spectrum(const double* moments, int nmoments, double a, double b,
                         int npoints, int kernel, double* omega_out, double* intensity_out);
 
 /*
+ * kpm_synchronize -- waits for all work queued on the context's stream and
+ * reports errors raised on the device: KPM_ETIMEOUT if a bounded wait inside a
+ * kernel ran out (the kernel then returned early and its output is invalid),
+ * KPM_ECUDA for an asynchronous CUDA error.
+ */
+kpm_status kpm_synchronize(kpm_ctx* ctx);
+
+/*
  * Per-launch timing of the H application inside the recursion.
  * kpm_profile_enable(ctx, 1): every H application queued by later
  * kpm_recursion_advance calls on ctx is bracketed by a CUDA event pair recorded

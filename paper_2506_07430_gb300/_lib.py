@@ -37,6 +37,7 @@ SIGNATURES = {
     "kpm_recursion_advance": (_I, [_P, _I]),
     "kpm_recursion_moments": (_I, [_P, _P, _P]),
     "kpm_spectrum": (_I, [_P, _I, _D, _D, _I, _I, _P, _P]),
+    "kpm_synchronize": (_I, [_P]),
     "kpm_profile_enable": (_I, [_P, _I]),
     "kpm_profile_read": (_I, [_P, _P, _P]),
     "kpm_launch_count": (_U64, []),
@@ -210,6 +211,9 @@ class KPM:
 
     def recursion_advance(self, nsteps: int):
         _check(self._lib().kpm_recursion_advance(self._h, nsteps), self._h)
+
+    def synchronize(self):
+        _check(self._lib().kpm_synchronize(self._h), self._h)
 
     def profile_enable(self, on: bool = True):
         _check(self._lib().kpm_profile_enable(self._h, 1 if on else 0), self._h)

@@ -20,7 +20,7 @@ struct kpm_ctx {
     int64_t dim = 0;
     std::string err = "no error";
 
-    DevBuf d_h1, d_eri, d_dip, d_V32;
+    DevBuf d_h1, d_eri, d_dip, d_V32, d_diag;
     SpinTables ta, tb_own;
     SpinTables* tb = nullptr;
     std::unique_ptr<TcSigma> tc;  // tensor-core sigma (KPM_MIXED)
@@ -121,7 +121,7 @@ void sigma_dispatch(kpm_ctx* c, const void* x, void* y, int ncol) {
         SigmaArgs a{&c->ta, c->tb, c->d_eri.p, c->n, c->dim};
         sigma_gather_f64(a, (const double*)x, (double*)y, ncol, c->st);
     } else if (c->prec == KPM_FP32) {
-        SigmaArgs a{&c->ta, c->tb, c->d_V32.p, c->n, c->dim};
+        SigmaArgs a{&c->ta, c->tb, c->d_V32.p, c->n, c->dim, c->d_diag.as<float2>()};
         sigma_gather_f32(a, (const float*)x, (float*)y, ncol, c->st);
     } else {
         c->tc->apply((const float*)x, (float*)y, ncol, c->st);
@@ -215,6 +215,11 @@ void rec_advance(kpm_ctx* c, int nsteps) {
     }
 }
 
+void check_device_errors(kpm_ctx* c) {
+    if (c->tc && c->tc->check(c->st))
+        KPM_THROW(KPM_ETIMEOUT, "a bounded wait in the tensor-core sigma kernel ran out");
+}
+
 kpm_status rec_collect(kpm_ctx* c, double* out, int nm_stride) {
     int ns = c->rec_steps;
     doubling_combine(c->dots.as<double>(), c->rec_ncol, ns, (int64_t)c->rec_max_steps * 2,
@@ -224,6 +229,7 @@ kpm_status rec_collect(kpm_ctx* c, double* out, int nm_stride) {
                                  c->moments_dev.as<double>() + (size_t)j * 2 * c->rec_max_steps,
                                  sizeof(double) * 2 * ns, cudaMemcpyDeviceToHost, c->st));
     KPM_CUDA(cudaStreamSynchronize(c->st));
+    check_device_errors(c);
     for (int j = 0; j < c->rec_ncol; ++j) {
         const double* m = out + (size_t)j * nm_stride;
         double lim = m[0] * (1.0 + 1e-6);
@@ -283,10 +289,12 @@ kpm_status kpm_create(const double* h1, const double* eri, const double* dipole,
         if (prec == KPM_FP32) {
             c->d_V32.alloc(n4 * 4);
             to_f32(c->d_eri.as<double>(), c->d_V32.as<float>(), n4, c->st);
+            c->d_diag.alloc((size_t)c->dim * sizeof(float2));
+            exact_diagonal(c->ta, *c->tb, c->d_eri.as<double>(), norb, c->d_diag.as<float2>(), c->st);
         }
         if (prec == KPM_MIXED) {
             c->tc.reset(new TcSigma());
-            c->tc->init(c->ta, *c->tb, h1, eri, norb, c->st);
+            c->tc->init(c->ta, *c->tb, c->d_h1.as<double>(), c->d_eri.as<double>(), norb, c->st);
         }
         KPM_CUDA(cudaStreamSynchronize(c->st));
     });
@@ -366,7 +374,7 @@ kpm_status kpm_bounds(kpm_ctx* ctx, int iters, uint64_t seed, double* emin, doub
         ctx->lz_v0.ensure(vb);
         ctx->lz_v1.ensure(vb);
         ctx->lz_w.ensure(vb);
-        ctx->lz_ab.ensure(sizeof(double) * 2 * (k + 1));
+        ctx->lz_ab.ensure(sizeof(double) * (5 * (k + 1)));
         ctx->lz_scalar.ensure(sizeof(double) * 8);
         ensure_reduce_scratch(ctx, 1);
         double* al = ctx->lz_ab.as<double>();
@@ -388,10 +396,11 @@ kpm_status kpm_bounds(kpm_ctx* ctx, int iters, uint64_t seed, double* emin, doub
             lanczos_scale(vp, w, ctx->dim, f64, sc, be + j, ctx->st);
             std::swap(v, vp);  // v <- v_{j+1}, vp <- v_j
         }
-        tridiag_extremes(al, be, k, sc + 2, ctx->st);
+        tridiag_extremes(al, be, k, sc + 2, be + (k + 1), ctx->st);
         double out4[4];
         KPM_CUDA(cudaMemcpyAsync(out4, sc + 2, sizeof(out4), cudaMemcpyDeviceToHost, ctx->st));
         KPM_CUDA(cudaStreamSynchronize(ctx->st));
+        check_device_errors(ctx);
         *emin = out4[0] - out4[2];
         *emax = out4[1] + out4[3];
     });
@@ -473,6 +482,16 @@ kpm_status kpm_spectrum(const double* moments, int nmoments, double a, double b,
                      dom.as<double>(), din.as<double>(), nullptr);
         KPM_CUDA(cudaMemcpy(omega_out, dom.p, sizeof(double) * npoints, cudaMemcpyDeviceToHost));
         KPM_CUDA(cudaMemcpy(intensity_out, din.p, sizeof(double) * npoints, cudaMemcpyDeviceToHost));
+    });
+}
+
+kpm_status kpm_synchronize(kpm_ctx* ctx) {
+    if (!ctx) { g_err = "NULL context"; return KPM_EINVAL; }
+    return guarded(ctx, [&] {
+        DeviceGuard g(ctx->device);
+        KPM_CUDA(cudaStreamSynchronize(ctx->st));
+        KPM_CUDA(cudaGetLastError());
+        check_device_errors(ctx);
     });
 }
 

@@ -115,7 +115,12 @@ struct SigmaArgs {
     const void* V;     // (pq|rs) as [n*n][n*n], double or float by path
     int n;
     int64_t dim;
+    const float2* diag = nullptr;  // FP32 path: exact diagonal H_II as (hi, lo)
 };
+
+// diag[I] = H_II (FP64 evaluation, stored as float hi + float lo).
+void exact_diagonal(const SpinTables& A, const SpinTables& B, const double* eri, int n,
+                    float2* diag, cudaStream_t st);
 
 void sigma_gather_f64(const SigmaArgs& a, const double* x, double* y, int ncol, cudaStream_t st);
 void sigma_gather_f32(const SigmaArgs& a, const float* x, float* y, int ncol, cudaStream_t st);
@@ -153,8 +158,9 @@ void lanczos_scale(void* vnext, const void* w, int64_t dim, bool f64, const doub
                    double* beta_out, cudaStream_t st);
 void fill_random(void* v, int64_t dim, bool f64, uint64_t seed, cudaStream_t st);
 void scale_inplace(void* v, int64_t dim, bool f64, const double* norm2, cudaStream_t st);
+// scratch: 3k doubles of device memory.
 void tridiag_extremes(const double* alpha, const double* beta, int k, double* out4,
-                      cudaStream_t st);
+                      double* scratch, cudaStream_t st);
 
 // Spectrum on the device: moments (device) -> omega, intensity (device);
 // `damped` is device scratch of N doubles (g_n Omega_n with the factor 2 for n >= 1).

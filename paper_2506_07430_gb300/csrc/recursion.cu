@@ -306,20 +306,41 @@ __device__ double tri_eig(const double* al, const double* be, int k, int idx, do
     return 0.5 * (lo + hi);
 }
 
-__device__ double last_component(const double* al, const double* be, int k, double th) {
-    double xm1 = 0.0, x = 1.0, nrm = 1.0;
-    for (int i = 0; i + 1 < k; ++i) {
-        if (be[i] == 0.0) return 0.0;
-        double xn = ((th - al[i]) * x - (i ? be[i - 1] * xm1 : 0.0)) / be[i];
-        xm1 = x;
-        x = xn;
-        nrm += x * x;
-        if (!isfinite(nrm) || nrm > 1e250) return 1.0;
+// Last component of the unit eigenvector of T for eigenvalue th, by inverse
+// iteration with the tridiagonal (Thomas) solver; w is scratch of 3k doubles.
+__device__ double last_component(const double* al, const double* be, int k, double th,
+                                 double* w) {
+    double* x = w;
+    double* c = w + k;
+    double* d = w + 2 * k;
+    double scale = 0.0;
+    for (int i = 0; i < k; ++i) scale = fmax(scale, fabs(al[i]) + (i + 1 < k ? fabs(be[i]) : 0.0));
+    const double shift = th + 1e-10 * (scale + 1e-300);
+    for (int i = 0; i < k; ++i) x[i] = 1.0;
+    for (int it = 0; it < 4; ++it) {
+        // solve (T - shift) y = x; y overwrites x
+        double piv = al[0] - shift;
+        if (fabs(piv) < 1e-300) piv = 1e-300;
+        c[0] = (k > 1 ? be[0] : 0.0) / piv;
+        d[0] = x[0] / piv;
+        for (int i = 1; i < k; ++i) {
+            piv = (al[i] - shift) - be[i - 1] * c[i - 1];
+            if (fabs(piv) < 1e-300) piv = 1e-300;
+            c[i] = (i + 1 < k ? be[i] : 0.0) / piv;
+            d[i] = (x[i] - be[i - 1] * d[i - 1]) / piv;
+        }
+        x[k - 1] = d[k - 1];
+        for (int i = k - 2; i >= 0; --i) x[i] = d[i] - c[i] * x[i + 1];
+        double nrm = 0.0;
+        for (int i = 0; i < k; ++i) nrm += x[i] * x[i];
+        nrm = sqrt(nrm);
+        if (!(nrm > 0.0) || !isfinite(nrm)) return 1.0;
+        for (int i = 0; i < k; ++i) x[i] /= nrm;
     }
-    return fabs(x) / sqrt(nrm);
+    return fabs(x[k - 1]);
 }
 
-__global__ void k_tridiag(const double* al, const double* be, int k, double* out) {
+__global__ void k_tridiag(const double* al, const double* be, int k, double* out, double* w) {
     if (threadIdx.x || blockIdx.x) return;
     double lo = al[0], hi = al[0];
     for (int i = 0; i < k; ++i) {
@@ -334,13 +355,13 @@ __global__ void k_tridiag(const double* al, const double* be, int k, double* out
     double bk = fabs(be[k - 1]);
     out[0] = tmin;
     out[1] = tmax;
-    out[2] = bk * last_component(al, be, k, tmin);
-    out[3] = bk * last_component(al, be, k, tmax);
+    out[2] = bk * last_component(al, be, k, tmin, w);
+    out[3] = bk * last_component(al, be, k, tmax, w);
 }
 
 void tridiag_extremes(const double* alpha, const double* beta, int k, double* out4,
-                      cudaStream_t st) {
-    k_tridiag<<<1, 1, 0, st>>>(alpha, beta, k, out4);
+                      double* scratch, cudaStream_t st) {
+    k_tridiag<<<1, 1, 0, st>>>(alpha, beta, k, out4, scratch);
     KPM_LAUNCHED();
 }
 

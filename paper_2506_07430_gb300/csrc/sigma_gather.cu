@@ -21,7 +21,13 @@
 
 namespace kpm {
 
-template <class T>
+// EXACT_DIAG (FP32 path): the diagonal H_II is taken from `diag` (FP64 value stored
+// as a float hi/lo pair) and every diagonal contribution is skipped in the
+// gathers: F entries t = 0 of both spins and the alpha-beta products whose alpha
+// and beta excitations are both diagonal (p == q).  Large diagonal energies
+// then carry no FP32 representation error, which would otherwise shift every
+// eigenvalue systematically and grow the moment error linearly in n.
+template <class T, bool EXACT_DIAG>
 __global__ void __launch_bounds__(128)
 k_sigma_gather(const T* __restrict__ x, T* __restrict__ y, int64_t nsa, int64_t nsb,
                const int32_t* __restrict__ tgtA, const uint16_t* __restrict__ pqA,
@@ -29,14 +35,16 @@ k_sigma_gather(const T* __restrict__ x, T* __restrict__ y, int64_t nsa, int64_t 
                const T* __restrict__ fvalA, int nnbrA, const int32_t* __restrict__ tgtBT,
                const uint16_t* __restrict__ pqBT, const int8_t* __restrict__ sgnBT, int nexcB,
                const int32_t* __restrict__ fcolB, const T* __restrict__ fvalB, int nnbrB,
-               const T* __restrict__ V, int n2) {
+               const T* __restrict__ V, int n, const float2* __restrict__ diag) {
     extern __shared__ __align__(16) unsigned char smem[];
     T* sFv = reinterpret_cast<T*>(smem);
     int32_t* sFc = reinterpret_cast<int32_t*>(sFv + nnbrA);
     int32_t* sJ = sFc + nnbrA;
     int32_t* sP = sJ + nexcA;
     int32_t* sS = sP + nexcA;
+    __shared__ int sNoff;
 
+    const int n2 = n * n;
     const int64_t ia = blockIdx.y;
     const int64_t ib = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t dim = nsa * nsb;
@@ -47,35 +55,63 @@ k_sigma_gather(const T* __restrict__ x, T* __restrict__ y, int64_t nsa, int64_t 
         sFv[t] = fvalA[(int64_t)t * nsa + ia];
         sFc[t] = fcolA[(int64_t)t * nsa + ia];
     }
-    for (int e = threadIdx.x; e < nexcA; e += blockDim.x) {
-        sJ[e] = tgtA[ia * nexcA + e];
-        sP[e] = pqA[ia * nexcA + e];
-        sS[e] = sgnA[ia * nexcA + e];
+    if (EXACT_DIAG) {
+        // alpha entries reordered: off-diagonal (p != q) first, then diagonal
+        if (threadIdx.x == 0) {
+            int k = 0;
+            for (int pass = 0; pass < 2; ++pass)
+                for (int e = 0; e < nexcA; ++e) {
+                    int g = pqA[ia * nexcA + e];
+                    bool dg = (g % (n + 1)) == 0;
+                    if (dg != (pass == 1)) continue;
+                    sJ[k] = tgtA[ia * nexcA + e];
+                    sP[k] = g;
+                    sS[k] = sgnA[ia * nexcA + e];
+                    ++k;
+                }
+            int noff = 0;
+            for (int e = 0; e < nexcA; ++e) noff += (pqA[ia * nexcA + e] % (n + 1)) != 0;
+            sNoff = noff;
+        }
+    } else {
+        for (int e = threadIdx.x; e < nexcA; e += blockDim.x) {
+            sJ[e] = tgtA[ia * nexcA + e];
+            sP[e] = pqA[ia * nexcA + e];
+            sS[e] = sgnA[ia * nexcA + e];
+        }
     }
     __syncthreads();
     if (ib >= nsb) return;
 
     const T* xrow = x + ia * nsb;
+    const int t0 = EXACT_DIAG ? 1 : 0;
     T acc = T(0);
     // same-spin beta: row I_a of x, columns = F_beta neighbours of I_b
-    for (int t = 0; t < nnbrB; ++t)
+    for (int t = t0; t < nnbrB; ++t)
         acc += fvalB[(int64_t)t * nsb + ib] * xrow[fcolB[(int64_t)t * nsb + ib]];
     // same-spin alpha: column I_b of x, rows = F_alpha neighbours of I_a
-    for (int t = 0; t < nnbrA; ++t) acc += sFv[t] * x[(int64_t)sFc[t] * nsb + ib];
+    for (int t = t0; t < nnbrA; ++t) acc += sFv[t] * x[(int64_t)sFc[t] * nsb + ib];
     // opposite-spin two-electron part
+    const int noff = EXACT_DIAG ? sNoff : nexcA;
     for (int f = 0; f < nexcB; ++f) {
         const int64_t jb = tgtBT[(int64_t)f * nsb + ib];
         const int pb = pqBT[(int64_t)f * nsb + ib];
         const T sb = T(sgnBT[(int64_t)f * nsb + ib]);
+        const int ne = (EXACT_DIAG && (pb % (n + 1)) == 0) ? noff : nexcA;
         T inner = T(0);
-        for (int e = 0; e < nexcA; ++e)
+        for (int e = 0; e < ne; ++e)
             inner += T(sS[e]) * V[(int64_t)sP[e] * n2 + pb] * x[(int64_t)sJ[e] * nsb + jb];
         acc += sb * inner;
+    }
+    if (EXACT_DIAG) {
+        const float2 d = diag[ia * nsb + ib];
+        const T xv = xrow[ib];
+        acc += fmaf(d.x, xv, d.y * xv);
     }
     y[ia * nsb + ib] = acc;
 }
 
-template <class T>
+template <class T, bool ED>
 static void launch_sigma(const SigmaArgs& a, const T* x, T* y, int ncol, const T* fvA,
                          const T* fvB, cudaStream_t st) {
     const SpinTables& A = *a.ta;
@@ -84,21 +120,64 @@ static void launch_sigma(const SigmaArgs& a, const T* x, T* y, int ncol, const T
     dim3 grid((unsigned)((B.ns + 127) / 128), (unsigned)A.ns, (unsigned)ncol);
     size_t sm = (size_t)A.nnbr * (sizeof(T) + 4) + (size_t)A.nexc * 12 + 16;
     if (sm > 48 * 1024)
-        KPM_CUDA(cudaFuncSetAttribute(k_sigma_gather<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)sm));
-    k_sigma_gather<T><<<grid, 128, sm, st>>>(
+        KPM_CUDA(cudaFuncSetAttribute(k_sigma_gather<T, ED>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_sigma_gather<T, ED><<<grid, 128, sm, st>>>(
         x, y, A.ns, B.ns, A.tgt.as<int32_t>(), A.pq.as<uint16_t>(), A.sgn.as<int8_t>(), A.nexc,
         A.fcol.as<int32_t>(), fvA, A.nnbr, B.tgtT.as<int32_t>(), B.pqT.as<uint16_t>(),
         B.sgnT.as<int8_t>(), B.nexc, B.fcol.as<int32_t>(), fvB, B.nnbr,
-        static_cast<const T*>(a.V), a.n * a.n);
+        static_cast<const T*>(a.V), a.n, a.diag);
     KPM_LAUNCHED();
 }
 
 void sigma_gather_f64(const SigmaArgs& a, const double* x, double* y, int ncol, cudaStream_t st) {
-    launch_sigma<double>(a, x, y, ncol, a.ta->fval64.as<double>(), a.tb->fval64.as<double>(), st);
+    launch_sigma<double, false>(a, x, y, ncol, a.ta->fval64.as<double>(),
+                                a.tb->fval64.as<double>(), st);
 }
 void sigma_gather_f32(const SigmaArgs& a, const float* x, float* y, int ncol, cudaStream_t st) {
-    launch_sigma<float>(a, x, y, ncol, a.ta->fval32.as<float>(), a.tb->fval32.as<float>(), st);
+    launch_sigma<float, true>(a, x, y, ncol, a.ta->fval32.as<float>(), a.tb->fval32.as<float>(),
+                              st);
+}
+
+// ---------------------------------------------------------------- exact diagonal
+
+// H_II = F_alpha[I_a,I_a] + F_beta[I_b,I_b] + sum_{i in I_a, j in I_b} (ii|jj), FP64,
+// stored as hi = float(H_II), lo = float(H_II - hi).
+__global__ void __launch_bounds__(128)
+k_diag(const uint32_t* __restrict__ maskA, const uint32_t* __restrict__ maskB, int64_t nsa,
+       int64_t nsb, const double* __restrict__ fA0, const double* __restrict__ fB0,
+       const double* __restrict__ eri, int n, float2* __restrict__ diag) {
+    __shared__ double v[KPM_MAX_ORB];
+    const int64_t ia = blockIdx.y;
+    const uint32_t Ia = maskA[ia];
+    if (threadIdx.x < n) {
+        int j = threadIdx.x;
+        double s = 0.0;
+        for (int i = 0; i < n; ++i)
+            if ((Ia >> i) & 1u) s += eri[(((int64_t)i * n + i) * n + j) * n + j];
+        v[j] = s;
+    }
+    __syncthreads();
+    const int64_t ib = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ib >= nsb) return;
+    uint32_t Ib = maskB[ib];
+    double d = fA0[ia] + fB0[ib];
+    while (Ib) {
+        int j = __ffs(Ib) - 1;
+        d += v[j];
+        Ib &= Ib - 1;
+    }
+    float hi = (float)d;
+    diag[ia * nsb + ib] = make_float2(hi, (float)(d - (double)hi));
+}
+
+void exact_diagonal(const SpinTables& A, const SpinTables& B, const double* eri, int n,
+                    float2* diag, cudaStream_t st) {
+    if (A.ns * B.ns == 0) return;
+    dim3 grid((unsigned)((B.ns + 127) / 128), (unsigned)A.ns);
+    k_diag<<<grid, 128, 0, st>>>(A.masks.as<uint32_t>(), B.masks.as<uint32_t>(), A.ns, B.ns,
+                                 A.fval64.as<double>(), B.fval64.as<double>(), eri, n, diag);
+    KPM_LAUNCHED();
 }
 
 // ---------------------------------------------------------------- dipole

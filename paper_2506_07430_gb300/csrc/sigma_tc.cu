@@ -1,14 +1,587 @@
+// sigma = H x with the two-electron contraction on tcgen05 tensor cores.
+//
+// Formulation.  With E_pq = E^a_pq + E^b_pq and k_pq = h_pq - 1/2 sum_r (pr|rq),
+// the paper's second-quantized H (Methods) is
+//   H = sum_pq k_pq E_pq + 1/2 sum_{pq,rs} (pq|rs) E_pq E_rs
+//     = [k E^b + 1/2 V E^b E^b + V E^a E^b] + [k E^a + 1/2 V E^a E^a],
+// using that alpha and beta excitations commute and (pq|rs) = (rs|pq).
+// Because (pq|rs) = (qp|rs) = (pq|sr), every sum over ordered pairs folds onto
+// the NS = n(n+1)/2 unordered pairs {p,q} ("slots").
+//
+// Row pass (rows = strings of the outer index R, columns = strings C; the
+// vector is X[R][C]).  For one row R and a tile of 128 columns J:
+//   A[J][s] = sum_{e in tab(R), slot(e)=s} sgn_e X[tgt_e, J]          (opposite spin)
+//           + 1/2 sum_{f in tab(J), slot(f)=s} sgn_f X[R, tgt_f]      (same spin, C side)
+//   A[J][NS] = X[R, J]                                              (one-body)
+//   G = A W,  W[s][s'] = (pq|rs) for s, s' < NS,  W[NS][s'] = k_{s'}
+//   sigma[R, tgt_f] += sgn_f G[J][slot(f)]   for every f in tab(J)  (scatter)
+// (<I|E_pq|J> = <J|E_qp|I> turns the outer excitation into a scatter from J.)
+// The first pass runs on X with R = alpha, C = beta and the opposite-spin part
+// on; the second on X^T with R = beta, C = alpha and the opposite-spin part
+// off; sigma = pass1 + (pass2)^T.  Every slot appears at most once in each
+// string's table, so A has at most two terms per entry.
+//
+// GEMM on the tensor cores: M = 128 columns J, N = K = P = NS+1 rounded up to a
+// multiple of 16.  A is written by the CUDA cores straight into tensor memory
+// (tcgen05.st, one TMEM lane per row J); W lives in shared memory (canonical
+// K-major layout without swizzle); D accumulates in tensor memory in FP32.
+// Operands are split into two 16-bit parts, x = hi + lo, and three MMAs
+// (A_hi W_hi + A_lo W_hi + A_hi W_lo) keep about 16 significant bits.
+// The epilogue reads D (tcgen05.ld) and scatters into the row's sigma held in
+// shared memory (shared-memory atomics), so nothing of G leaves the chip.
+//
+// One CTA (256 threads) per SM, persistent over rows.  Warps w and w+4 share
+// TMEM lane quadrant w%4 (rows 32(w%4)..+31) and split the slots in halves.
+// A is double-buffered in TMEM so that building the A of tile t+1 overlaps the
+// MMAs of tile t.  Waits on the MMA-completion mbarrier are bounded (about one
+// second); on expiry the kernel records an error, frees its TMEM and returns.
 #include "sigma_tc.cuh"
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 namespace kpm {
 
-void TcSigma::init(const SpinTables&, const SpinTables&, const double*, const double*, int,
-                   cudaStream_t) {
-    KPM_THROW(KPM_EUNSUPPORTED, "KPM_MIXED is not available in this build");
+namespace {
+
+constexpr int TC_THREADS = 256;
+constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-void TcSigma::apply(const float*, float*, int, cudaStream_t) {
-    KPM_THROW(KPM_EUNSUPPORTED, "KPM_MIXED is not available in this build");
+__device__ __forceinline__ void tmem_alloc(uint32_t* holder, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32(holder)), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, uint32_t a, uint32_t b, uint32_t c,
+                                         uint32_t d) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};"
+                 ::"r"(taddr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld_wait() {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+// D[tmem] (+)= A[tmem] * B[smem]^T, kind::f16 (BF16 or FP16 operands, FP32 accumulate)
+__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}"
+        ::"r"(d), "r"(a), "l"(bdesc), "r"(idesc), "r"(accumulate) : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* mbar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+        ::"r"(smem_u32(mbar)) : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(mbar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Shared-memory matrix descriptor, canonical K-major layout without swizzle:
+// 8-row x 16-byte core matrices; LBO = byte distance between core matrices
+// adjacent along K, SBO = between core matrices adjacent along M/N.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+    return d;                // base offset 0, swizzle none
+}
+
+// Instruction descriptor, kind::f16: D = F32, A/B = BF16 (1) or F16 (0), both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N, bool bf16) {
+    return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+template <bool FP16>
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+    if (FP16) {
+        __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<uint32_t*>(&h);
+    } else {
+        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<uint32_t*>(&h);
+    }
+}
+template <bool FP16>
+__device__ __forceinline__ float round16(float a) {
+    if (FP16) return __half2float(__float2half_rn(a));
+    return __bfloat162float(__float2bfloat16_rn(a));
+}
+
+__device__ __forceinline__ void slot_pair(int s, int& p, int& q) {
+    // s = q (q + 1) / 2 + p, 0 <= p <= q
+    q = (int)((sqrtf(8.0f * s + 1.0f) - 1.0f) * 0.5f);
+    while ((q + 1) * (q + 2) / 2 <= s) ++q;
+    while (q * (q + 1) / 2 > s) --q;
+    p = s - q * (q + 1) / 2;
+}
+
+struct RowPass {
+    const float* X;
+    float* Y;
+    int64_t Nr, Nc;
+    const uint16_t* tslot;   // [P][Nc]
+    const uint32_t* cmask;   // [Nc]
+    const int32_t* rtgt;     // [Nr][rnexc] row-string tables (opposite-spin part)
+    const uint16_t* rpq;
+    const int8_t* rsgn;
+    int rnexc;               // 0: opposite-spin part off
+    const uint4* wimg;       // W image, hi then lo, 4 P^2 bytes
+    int P, NS, n;
+    uint32_t ncols;          // TMEM columns allocated
+    float scale, inv_scale;  // FP16 operand scaling of A (power of two)
+    int* err;
+};
+
+template <bool FP16>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_rowpass(const RowPass p) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int P = p.P, NS = p.NS;
+    const int64_t Nc = p.Nc;
+    uint8_t* sB = smem;
+    float* xrow = reinterpret_cast<float*>(smem + 4 * P * P);
+    float* srow = xrow + Nc;
+    int32_t* rowmap = reinterpret_cast<int32_t*>(srow + Nc);
+    uint32_t* betw = reinterpret_cast<uint32_t*>(rowmap + P);
+    uintptr_t tail = (reinterpret_cast<uintptr_t>(betw + P) + 15) & ~uintptr_t(15);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(tail);
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(mbar + 1);
+    int* abort_flag = reinterpret_cast<int*>(tmem_holder + 1);
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int quad = warp & 3, half = warp >> 2;
+    const int m = quad * 32 + lane;
+    const int slot0 = half * (P / 2), slot1 = slot0 + P / 2;
+
+    {
+        const int nv = (P * P) / 4;  // uint4 count of 4 P^2 bytes
+        uint4* dst = reinterpret_cast<uint4*>(sB);
+        for (int i = tid; i < nv; i += TC_THREADS) dst[i] = p.wimg[i];
+    }
+    for (int s = tid; s < P; s += TC_THREADS) {
+        uint32_t bm = 0;
+        if (s < NS) {
+            int a, b;
+            slot_pair(s, a, b);  // a <= b
+            if (a != b) bm = ((1u << b) - 1u) & ~((2u << a) - 1u);
+        }
+        betw[s] = bm;
+    }
+    if (tid == 0) {
+        mbar_init(mbar, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(tmem_holder, p.ncols);
+        tmem_relinquish();
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tmem_holder;
+    const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
+    const uint32_t idesc = instr_desc(128, P, !FP16);
+    const uint32_t sB_addr = smem_u32(sB);
+    const uint32_t SBO = 16u * (uint32_t)P, LBO = 128u;
+    const int ntiles = (int)((Nc + 127) / 128);
+    const float sc = p.scale, isc = p.inv_scale;
+    uint32_t phase = 0;
+
+    auto slot_value = [&](int s, int64_t jc, uint32_t cm, int64_t ir) -> float {
+        float v = 0.f;
+        if (s < NS) {
+            const int rm = rowmap[s];
+            if (rm >= 0) {
+                float xv = __ldg(p.X + (int64_t)(rm >> 1) * Nc + jc);
+                v = (rm & 1) ? -xv : xv;
+            }
+            const uint16_t tg = __ldg(p.tslot + (int64_t)s * Nc + jc);
+            if (tg != 0xFFFFu) {
+                float xv = 0.5f * xrow[tg];
+                v += (__popc(cm & betw[s]) & 1) ? -xv : xv;
+            }
+        } else if (s == NS) {
+            v = xrow[jc];
+        }
+        return v * sc;
+    };
+
+    auto build = [&](int t, int buf, int64_t ir) {
+        const int64_t jc = (int64_t)t * 128 + m;
+        const bool valid = jc < Nc;
+        const uint32_t cm = valid ? __ldg(p.cmask + jc) : 0u;
+        const uint32_t a_hi = tbase + lane_base + (uint32_t)(buf * P);
+        const uint32_t a_lo = a_hi + (uint32_t)(P / 2);
+        for (int c0 = slot0; c0 < slot1; c0 += 8) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = valid ? slot_value(c0 + u, jc, cm, ir) : 0.f;
+            uint32_t hi[4], lo[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                float h0 = round16<FP16>(v[2 * u]), h1 = round16<FP16>(v[2 * u + 1]);
+                hi[u] = pack2<FP16>(h0, h1);
+                lo[u] = pack2<FP16>(v[2 * u] - h0, v[2 * u + 1] - h1);
+            }
+            tmem_st4(a_hi + (uint32_t)(c0 / 2), hi[0], hi[1], hi[2], hi[3]);
+            tmem_st4(a_lo + (uint32_t)(c0 / 2), lo[0], lo[1], lo[2], lo[3]);
+        }
+    };
+
+    auto issue = [&](int t) {
+        const int buf = t & 1;
+        const uint32_t a_hi = tbase + (uint32_t)(buf * P);
+        const uint32_t a_lo = a_hi + (uint32_t)(P / 2);
+        const uint32_t d = tbase + (uint32_t)(2 * P);
+        const int ksteps = P / 16;
+        for (int pass = 0; pass < 3; ++pass) {
+            const uint32_t a = (pass == 1) ? a_lo : a_hi;
+            const uint32_t bbase = sB_addr + (pass == 2 ? (uint32_t)(2 * P * P) : 0u);
+            for (int j = 0; j < ksteps; ++j) {
+                uint64_t bd = smem_desc(bbase + (uint32_t)(j * 256), LBO, SBO);
+                mma_ts(d, a + (uint32_t)(j * 8), bd, idesc, (pass | j) != 0);
+            }
+        }
+        mma_commit(mbar);
+    };
+
+    auto epilogue = [&](int t) {
+        const int64_t jc = (int64_t)t * 128 + m;
+        const bool valid = jc < Nc;
+        const uint32_t cm = valid ? __ldg(p.cmask + jc) : 0u;
+        const uint32_t dcol = tbase + lane_base + (uint32_t)(2 * P);
+        for (int c0 = slot0; c0 < slot1; c0 += 8) {
+            uint32_t r[8];
+            tmem_ld8(dcol + (uint32_t)c0, r);
+            tmem_ld_wait();
+            if (valid) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int s = c0 + u;
+                    if (s < NS) {
+                        const uint16_t tg = __ldg(p.tslot + (int64_t)s * Nc + jc);
+                        if (tg != 0xFFFFu) {
+                            float g = __uint_as_float(r[u]) * isc;
+                            if (__popc(cm & betw[s]) & 1) g = -g;
+                            atomicAdd(srow + tg, g);
+                        }
+                    }
+                }
+            }
+        }
+    };
+
+    for (int64_t ir = blockIdx.x; ir < p.Nr; ir += gridDim.x) {
+        for (int64_t j = tid; j < Nc; j += TC_THREADS) {
+            xrow[j] = p.X[ir * Nc + j];
+            srow[j] = 0.f;
+        }
+        for (int s = tid; s < P; s += TC_THREADS) rowmap[s] = -1;
+        __syncthreads();
+        for (int e = tid; e < p.rnexc; e += TC_THREADS) {
+            const int g = p.rpq[ir * p.rnexc + e];
+            int a = g / p.n, b = g % p.n;
+            if (a > b) { int t = a; a = b; b = t; }
+            const int s = b * (b + 1) / 2 + a;
+            rowmap[s] = (p.rtgt[ir * p.rnexc + e] << 1) | (p.rsgn[ir * p.rnexc + e] < 0 ? 1 : 0);
+        }
+        __syncthreads();
+
+        build(0, 0, ir);
+        tmem_st_wait();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            issue(0);
+        }
+        for (int t = 0; t < ntiles; ++t) {
+            if (t + 1 < ntiles) build(t + 1, (t + 1) & 1, ir);
+            if (tid == 0) {
+                long long t0 = clock64();
+                while (!mbar_try_wait(mbar, phase)) {
+                    if (clock64() - t0 > WAIT_CYCLES) {
+                        *abort_flag = 1;
+                        atomicExch(p.err, 1);
+                        break;
+                    }
+                }
+            }
+            phase ^= 1u;
+            __syncthreads();
+            if (*abort_flag) break;
+            tc_fence_after();
+            epilogue(t);
+            tmem_st_wait();
+            tc_fence_before();
+            __syncthreads();
+            if (t + 1 < ntiles && tid == 0) {
+                tc_fence_after();
+                issue(t + 1);
+            }
+        }
+        __syncthreads();
+        if (*abort_flag) break;
+        for (int64_t j = tid; j < Nc; j += TC_THREADS) p.Y[ir * Nc + j] = srow[j];
+        __syncthreads();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tbase, p.ncols);
+}
+
+// ---------------------------------------------------------------- set-up kernels
+
+// W image: B operand of the MMA is W^T (N = output slot, K = input slot) in the
+// canonical K-major layout; element (nr, kc) at (nr/8)*16P + (kc/8)*128 +
+// (nr%8)*16 + (kc%8)*2 bytes.  hi = round(W), lo = round(W - hi).
+template <bool FP16>
+__global__ void k_wimg(const double* __restrict__ h1, const double* __restrict__ eri, int n,
+                       int P, int NS, uint8_t* __restrict__ img, double wscale) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= P * P) return;
+    const int nr = idx / P;  // output slot
+    const int kc = idx % P;  // input slot
+    double w = 0.0;
+    if (nr < NS) {
+        int po, qo;
+        slot_pair(nr, po, qo);
+        if (kc < NS) {
+            int pi, qi;
+            slot_pair(kc, pi, qi);
+            w = eri[(((int64_t)pi * n + qi) * n + po) * n + qo];
+        } else if (kc == NS) {
+            double k = h1[po * n + qo];
+            for (int r = 0; r < n; ++r) k -= 0.5 * eri[(((int64_t)po * n + r) * n + r) * n + qo];
+            w = k;
+        }
+    }
+    w *= wscale;
+    float hi_f, lo_f;
+    uint16_t hb, lb;
+    if (FP16) {
+        __half h = __double2half(w);
+        hi_f = __half2float(h);
+        __half l = __double2half(w - (double)hi_f);
+        hb = *reinterpret_cast<uint16_t*>(&h);
+        lb = *reinterpret_cast<uint16_t*>(&l);
+    } else {
+        __nv_bfloat16 h = __double2bfloat16(w);
+        hi_f = __bfloat162float(h);
+        __nv_bfloat16 l = __double2bfloat16(w - (double)hi_f);
+        hb = *reinterpret_cast<uint16_t*>(&h);
+        lb = *reinterpret_cast<uint16_t*>(&l);
+    }
+    (void)lo_f;
+    const size_t off = (size_t)(nr / 8) * (16 * P) + (size_t)(kc / 8) * 128 + (nr % 8) * 16 +
+                       (kc % 8) * 2;
+    *reinterpret_cast<uint16_t*>(img + off) = hb;
+    *reinterpret_cast<uint16_t*>(img + 2 * (size_t)P * P + off) = lb;
+}
+
+// slot table: for string j and its entry (pq -> tgt), slot {p,q} -> tgt.
+__global__ void k_slot_table(const int32_t* __restrict__ tgt, const uint16_t* __restrict__ pq,
+                             int64_t ns, int nexc, int n, uint16_t* __restrict__ tslot) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ns * nexc) return;
+    const int64_t j = i / nexc;
+    int a = pq[i] / n, b = pq[i] % n;
+    if (a > b) { int t = a; a = b; b = t; }
+    const int s = b * (b + 1) / 2 + a;
+    tslot[(int64_t)s * ns + j] = (uint16_t)tgt[i];
+}
+
+// out[c][r] = in[r][c] for an R x C matrix.
+__global__ void k_transpose(const float* __restrict__ in, float* __restrict__ out, int64_t R,
+                            int64_t C) {
+    __shared__ float t[32][33];
+    const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        int64_t r = r0 + k, c = c0 + threadIdx.x;
+        if (r < R && c < C) t[k][threadIdx.x] = in[r * C + c];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        int64_t c = c0 + k, r = r0 + threadIdx.x;
+        if (r < R && c < C) out[c * R + r] = t[threadIdx.x][k];
+    }
+}
+
+// y[r][c] += sp[c][r] for an R x C matrix y.
+__global__ void k_add_transposed(float* __restrict__ y, const float* __restrict__ sp, int64_t R,
+                                 int64_t C) {
+    __shared__ float t[32][33];
+    const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        int64_t c = c0 + k, r = r0 + threadIdx.x;
+        if (r < R && c < C) t[k][threadIdx.x] = sp[c * R + r];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        int64_t r = r0 + k, c = c0 + threadIdx.x;
+        if (r < R && c < C) y[r * C + c] += t[threadIdx.x][k];
+    }
+}
+
+uint32_t tmem_cols(int P) {
+    uint32_t need = (uint32_t)(3 * P), c = 32;
+    while (c < need) c <<= 1;
+    return c;
+}
+
+size_t rowpass_smem(int P, int64_t Nc) {
+    return (size_t)4 * P * P + 8 * (size_t)Nc + 8 * (size_t)P + 64;
+}
+
+}  // namespace
+
+void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
+                   const double* d_eri, int norb, cudaStream_t st) {
+    ta = &A;
+    tb = &B;
+    n = norb;
+    NS = n * (n + 1) / 2;
+    P = ((NS + 1 + 15) / 16) * 16;
+    nsa = A.ns;
+    nsb = B.ns;
+    dim = nsa * nsb;
+    fp16 = false;
+    if (tmem_cols(P) > 512)
+        KPM_THROW(KPM_EUNSUPPORTED, "KPM_MIXED supports up to 17 orbitals (tensor memory)");
+    int dev = 0;
+    KPM_CUDA(cudaGetDevice(&dev));
+    cudaDeviceProp prop;
+    KPM_CUDA(cudaGetDeviceProperties(&prop, dev));
+    if (prop.major != 10)
+        KPM_THROW(KPM_EUNSUPPORTED, "KPM_MIXED needs a Blackwell (sm_10x) GPU");
+    nsm = prop.multiProcessorCount;
+    int64_t ncmax = nsa > nsb ? nsa : nsb;
+    smem_bytes = rowpass_smem(P, ncmax);
+    // at least ~116 KB so that exactly one CTA (and one TMEM allocation) fits per SM
+    size_t floor_bytes = 116 * 1024;
+    if (smem_bytes < floor_bytes) smem_bytes = floor_bytes;
+    if (smem_bytes > (size_t)prop.sharedMemPerBlockOptin)
+        KPM_THROW(KPM_EUNSUPPORTED, "KPM_MIXED: row of %lld strings needs %zu B shared memory",
+                  (long long)ncmax, smem_bytes);
+    KPM_CUDA(cudaFuncSetAttribute(k_rowpass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_bytes));
+    KPM_CUDA(cudaFuncSetAttribute(k_rowpass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_bytes));
+
+    wimg.alloc((size_t)4 * P * P);
+    KPM_CUDA(cudaMemsetAsync(wimg.p, 0, (size_t)4 * P * P, st));
+    if (fp16)
+        k_wimg<true><<<(P * P + 255) / 256, 256, 0, st>>>(d_h1, d_eri, n, P, NS, wimg.as<uint8_t>(), 1.0);
+    else
+        k_wimg<false><<<(P * P + 255) / 256, 256, 0, st>>>(d_h1, d_eri, n, P, NS, wimg.as<uint8_t>(), 1.0);
+    KPM_LAUNCHED();
+
+    auto build_slots = [&](const SpinTables& T, DevBuf& out) {
+        size_t bytes = (size_t)P * T.ns * sizeof(uint16_t);
+        out.alloc(bytes);
+        KPM_CUDA(cudaMemsetAsync(out.p, 0xFF, bytes, st));
+        int64_t ne = T.ns * T.nexc;
+        if (ne > 0) {
+            k_slot_table<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
+                T.tgt.as<int32_t>(), T.pq.as<uint16_t>(), T.ns, T.nexc, n, out.as<uint16_t>());
+            KPM_LAUNCHED();
+        }
+    };
+    build_slots(A, slot_a);
+    build_slots(B, slot_b);
+    xt.alloc((size_t)dim * sizeof(float));
+    sp.alloc((size_t)dim * sizeof(float));
+    err.alloc(sizeof(int));
+    KPM_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+}
+
+void TcSigma::apply(const float* x, float* y, int ncol, cudaStream_t st) {
+    const uint32_t nc = tmem_cols(P);
+    for (int c = 0; c < ncol; ++c) {
+        const float* X = x + (size_t)c * dim;
+        float* Y = y + (size_t)c * dim;
+        // pass 1: rows alpha, columns beta, opposite-spin part on
+        RowPass p1{X, Y, nsa, nsb, slot_b.as<uint16_t>(), tb->masks.as<uint32_t>(),
+                   ta->tgt.as<int32_t>(), ta->pq.as<uint16_t>(), ta->sgn.as<int8_t>(), ta->nexc,
+                   wimg.as<uint4>(), P, NS, n, nc, 1.0f, 1.0f, err.as<int>()};
+        int g1 = (int)(nsa < nsm ? nsa : nsm);
+        if (fp16) k_rowpass<true><<<g1, TC_THREADS, smem_bytes, st>>>(p1);
+        else k_rowpass<false><<<g1, TC_THREADS, smem_bytes, st>>>(p1);
+        KPM_LAUNCHED();
+        // pass 2 on x^T: rows beta, columns alpha, same-spin alpha part only
+        dim3 tb2(32, 8);
+        dim3 gt((unsigned)((nsb + 31) / 32), (unsigned)((nsa + 31) / 32));
+        k_transpose<<<gt, tb2, 0, st>>>(X, xt.as<float>(), nsa, nsb);
+        KPM_LAUNCHED();
+        RowPass p2{xt.as<float>(), sp.as<float>(), nsb, nsa, slot_a.as<uint16_t>(),
+                   ta->masks.as<uint32_t>(), nullptr, nullptr, nullptr, 0, wimg.as<uint4>(), P,
+                   NS, n, nc, 1.0f, 1.0f, err.as<int>()};
+        int g2 = (int)(nsb < nsm ? nsb : nsm);
+        if (fp16) k_rowpass<true><<<g2, TC_THREADS, smem_bytes, st>>>(p2);
+        else k_rowpass<false><<<g2, TC_THREADS, smem_bytes, st>>>(p2);
+        KPM_LAUNCHED();
+        k_add_transposed<<<gt, tb2, 0, st>>>(Y, sp.as<float>(), nsa, nsb);
+        KPM_LAUNCHED();
+    }
+}
+
+int TcSigma::check(cudaStream_t st) {
+    int h = 0;
+    KPM_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KPM_CUDA(cudaStreamSynchronize(st));
+    if (h) KPM_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+    return h;
 }
 
 }  // namespace kpm

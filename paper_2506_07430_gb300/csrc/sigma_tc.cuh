@@ -4,10 +4,26 @@
 
 namespace kpm {
 
+// sigma = H x with the two-electron terms contracted on the 5th-generation
+// tensor cores.  See sigma_tc.cu for the formulation.
 struct TcSigma {
-    void init(const SpinTables& ta, const SpinTables& tb, const double* h1_host,
-              const double* eri_host, int n, cudaStream_t st);
+    int n = 0, NS = 0, P = 0;     // orbitals, unordered pairs n(n+1)/2, padded K = N
+    int64_t nsa = 0, nsb = 0, dim = 0;
+    int nsm = 0;                  // SMs of the device (persistent grid)
+    bool fp16 = false;            // operand format: split FP16 (scaled) or split BF16
+    const SpinTables* ta = nullptr;
+    const SpinTables* tb = nullptr;
+    DevBuf wimg;                  // W = [(pq|rs) ; k] as split 16-bit operand image (hi | lo)
+    DevBuf slot_a, slot_b;        // uint16 [P][N_s] pair-slot -> target string (0xFFFF: none)
+    DevBuf xt, sp;                // workspaces: x transposed, transposed-pass output
+    DevBuf err;                   // int error flag (1: a bounded wait ran out)
+    size_t smem_bytes = 0;
+
+    void init(const SpinTables& ta, const SpinTables& tb, const double* d_h1,
+              const double* d_eri, int n, cudaStream_t st);
     void apply(const float* x, float* y, int ncol, cudaStream_t st);
+    // Reads and clears the device error flag (synchronises the stream).
+    int check(cudaStream_t st);
 };
 
 }  // namespace kpm
