@@ -49,7 +49,7 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="fci16o16e")
-    p.add_argument("--precision", choices=["fp64", "fp32", "mixed"], default="fp32")
+    p.add_argument("--precision", choices=["fp64", "fp32", "mixed", "mixed_bf16"], default="fp32")
     p.add_argument("--chunk", type=int, default=None, help="Chebyshev steps per bench step")
     p.add_argument("--lanczos", type=int, default=24, help="Lanczos steps for a, b (untimed)")
     p.add_argument("--e2e-requests", type=int, default=2)
@@ -227,8 +227,8 @@ def run_ours(args, ws, rank, local, pg):
     torch.cuda.set_device(local)
     w = synthetic.workload(args.workload)
     n, na, nb = w["norb"], w["nalpha"], w["nbeta"]
-    chunk = args.chunk or {"fp64": 1, "fp32": 1, "mixed": 16}[args.precision]
-    steps = args.steps or {"fp64": 4, "fp32": 8, "mixed": 8}[args.precision]
+    chunk = args.chunk or {"fp64": 1, "fp32": 1, "mixed": 16, "mixed_bf16": 16}[args.precision]
+    steps = args.steps or {"fp64": 4, "fp32": 8, "mixed": 8, "mixed_bf16": 8}[args.precision]
     warm = max(3, args.warmup)
     I = synthetic.integrals(n, na, nb, w["seed"])
     k = KPM(I.h1, I.eri, I.dipole, n, na, nb, precision=args.precision)
@@ -279,7 +279,7 @@ def run_ours(args, ws, rank, local, pg):
     flops = step_flops(w, nexc, nnbr)
     per_launch_s = (sig_ms / max(sig_cnt, 1)) / 1e3
     achieved = flops / per_launch_s / 1e12
-    if args.precision == "mixed":
+    if args.precision in ("mixed", "mixed_bf16"):
         bound, peak = "tensor", float(peaks.get("bf16_tflops_sustained", 1735.0))
         peak_note = f"bf16 dense sustained, {peak_src}"
     else:
@@ -318,7 +318,8 @@ def run_ours(args, ws, rank, local, pg):
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": steps,
         "warmup": warm, "ms_per_step": round(ms_max / steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "bf16x3-f32acc"}[args.precision],
+        "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "fp16x(2,3)-f32acc",
+                  "mixed_bf16": "bf16x2-f32acc"}[args.precision],
         "data": "synthetic (seeded integrals, seeded normalised state in place of the NQS ground state)",
         "config": {"workload": args.workload, "norb": n, "nalpha": na, "nbeta": nb, "dim": dim,
                    "nmoments": w["nmoments"], "chebyshev_steps_per_bench_step": chunk,

@@ -66,10 +66,15 @@ typedef enum {
 } kpm_status;
 
 typedef enum {
-    KPM_FP64 = 0,   /* FP64 vectors and arithmetic everywhere (reference path)      */
-    KPM_FP32 = 1,   /* FP32 vectors and FP32 CUDA-core sigma; FP64 dots/moments      */
-    KPM_MIXED = 2   /* FP32 vectors; two-electron sigma on tensor cores (tcgen05,
-                       split-BF16 operands, FP32 accumulation); FP64 dots/moments   */
+    KPM_FP64 = 0,      /* FP64 vectors and arithmetic everywhere (reference path)     */
+    KPM_FP32 = 1,      /* FP32 vectors, FP32 CUDA-core sigma with the diagonal H_II
+                          evaluated in FP64; FP64 dots/moments                        */
+    KPM_MIXED = 2,     /* FP32 vectors; two-electron sigma on tensor cores (tcgen05):
+                          operands split into FP16 pieces with power-of-two scaling
+                          (x in 2, integrals in 3 pieces, 4 MMAs, FP32 accumulation);
+                          FP64 dots/moments; up to 16 orbitals                       */
+    KPM_MIXED_BF16 = 3 /* as KPM_MIXED with split-BF16 operands (2 pieces each,
+                          3 MMAs): ~16 significant bits per product                  */
 } kpm_precision;
 
 /* Largest orbital count this build supports (strings are 32-bit masks, string

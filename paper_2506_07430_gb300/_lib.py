@@ -14,7 +14,7 @@ KPM_OK, KPM_EINVAL, KPM_ENOMEM, KPM_ECUDA, KPM_EBOUNDS, KPM_ETIMEOUT, KPM_ECANCE
     KPM_EUNSUPPORTED = range(8)
 _STATUS = {0: "KPM_OK", 1: "KPM_EINVAL", 2: "KPM_ENOMEM", 3: "KPM_ECUDA", 4: "KPM_EBOUNDS",
            5: "KPM_ETIMEOUT", 6: "KPM_ECANCELLED", 7: "KPM_EUNSUPPORTED"}
-PRECISIONS = {"fp64": 0, "fp32": 1, "mixed": 2}
+PRECISIONS = {"fp64": 0, "fp32": 1, "mixed": 2, "mixed_bf16": 3}
 
 # Every function declared in include/kpm.h with (restype, argtypes).
 _P, _I, _I64, _U, _U64, _D = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint,

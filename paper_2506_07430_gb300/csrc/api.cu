@@ -257,7 +257,7 @@ kpm_status kpm_create(const double* h1, const double* eri, const double* dipole,
             KPM_THROW(KPM_EINVAL, "norb must be in 1..%d", KPM_MAX_ORB);
         if (nalpha < 0 || nbeta < 0 || nalpha > norb || nbeta > norb)
             KPM_THROW(KPM_EINVAL, "electron counts must be in 0..norb");
-        if (prec != KPM_FP64 && prec != KPM_FP32 && prec != KPM_MIXED)
+        if (prec != KPM_FP64 && prec != KPM_FP32 && prec != KPM_MIXED && prec != KPM_MIXED_BF16)
             KPM_THROW(KPM_EINVAL, "unknown precision %d", (int)prec);
         check_sym(h1, norb, "h1");
         for (int cc = 0; cc < 3; ++cc) check_sym(dipole + (size_t)cc * norb * norb, norb, "dipole");
@@ -292,9 +292,19 @@ kpm_status kpm_create(const double* h1, const double* eri, const double* dipole,
             c->d_diag.alloc((size_t)c->dim * sizeof(float2));
             exact_diagonal(c->ta, *c->tb, c->d_eri.as<double>(), norb, c->d_diag.as<float2>(), c->st);
         }
-        if (prec == KPM_MIXED) {
+        if (prec == KPM_MIXED || prec == KPM_MIXED_BF16) {
+            double wmax = 0.0;
+            for (int64_t i = 0; i < n4; ++i) wmax = std::fmax(wmax, std::fabs(eri[i]));
+            for (int p = 0; p < norb; ++p)
+                for (int q = 0; q < norb; ++q) {
+                    double k = h1[p * norb + q];
+                    for (int r = 0; r < norb; ++r)
+                        k -= 0.5 * eri[(((int64_t)p * norb + r) * norb + r) * norb + q];
+                    wmax = std::fmax(wmax, std::fabs(k));
+                }
             c->tc.reset(new TcSigma());
-            c->tc->init(c->ta, *c->tb, c->d_h1.as<double>(), c->d_eri.as<double>(), norb, c->st);
+            c->tc->init(c->ta, *c->tb, c->d_h1.as<double>(), c->d_eri.as<double>(), norb, wmax,
+                        prec == KPM_MIXED, c->st);
         }
         KPM_CUDA(cudaStreamSynchronize(c->st));
     });

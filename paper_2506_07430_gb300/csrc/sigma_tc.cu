@@ -40,6 +40,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <cmath>
+
 namespace kpm {
 
 namespace {
@@ -168,26 +170,31 @@ struct RowPass {
     const float* X;
     float* Y;
     int64_t Nr, Nc;
-    const uint16_t* tslot;   // [P][Nc]
+    const uint32_t* tslot2;  // [P/2][Nc]: targets of slots 2i (low 16 bits) and 2i+1
     const uint32_t* cmask;   // [Nc]
     const int32_t* rtgt;     // [Nr][rnexc] row-string tables (opposite-spin part)
     const uint16_t* rpq;
     const int8_t* rsgn;
     int rnexc;               // 0: opposite-spin part off
-    const uint4* wimg;       // W image, hi then lo, 4 P^2 bytes
-    int P, NS, n;
+    const uint4* wimg;       // W image: NW pieces of 2 P^2 bytes each
+    int NS, n;
     uint32_t ncols;          // TMEM columns allocated
-    float scale, inv_scale;  // FP16 operand scaling of A (power of two)
+    const float* amax;       // device max|X| (FP16 operand scaling), or nullptr
+    float wscale;            // power-of-two scale applied to W in the image
     int* err;
 };
 
-template <bool FP16>
+// P: padded K = N (multiple of 16); FP16: operand format (else BF16);
+// NW: number of 16-bit pieces of W (2 or 3).  MMA passes: A_hi W_j for every
+// piece j, plus A_lo W_0.
+template <int P, bool FP16, int NW>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_rowpass(const RowPass p) {
+    constexpr int NH = P / 2;  // slots per half
     extern __shared__ __align__(1024) unsigned char smem[];
-    const int P = p.P, NS = p.NS;
+    const int NS = p.NS;
     const int64_t Nc = p.Nc;
     uint8_t* sB = smem;
-    float* xrow = reinterpret_cast<float*>(smem + 4 * P * P);
+    float* xrow = reinterpret_cast<float*>(smem + 2 * NW * P * P);
     float* srow = xrow + Nc;
     int32_t* rowmap = reinterpret_cast<int32_t*>(srow + Nc);
     uint32_t* betw = reinterpret_cast<uint32_t*>(rowmap + P);
@@ -200,10 +207,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_rowpass(const RowPass p) {
     const int warp = tid >> 5, lane = tid & 31;
     const int quad = warp & 3, half = warp >> 2;
     const int m = quad * 32 + lane;
-    const int slot0 = half * (P / 2), slot1 = slot0 + P / 2;
+    const int slot0 = half * NH;
 
     {
-        const int nv = (P * P) / 4;  // uint4 count of 4 P^2 bytes
+        constexpr int nv = (2 * NW * P * P) / 16;
         uint4* dst = reinterpret_cast<uint4*>(sB);
         for (int i = tid; i < nv; i += TC_THREADS) dst[i] = p.wimg[i];
     }
@@ -231,51 +238,83 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_rowpass(const RowPass p) {
     tc_fence_after();
     const uint32_t tbase = *tmem_holder;
     const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
-    const uint32_t idesc = instr_desc(128, P, !FP16);
+    constexpr uint32_t idesc = instr_desc(128, P, !FP16);
     const uint32_t sB_addr = smem_u32(sB);
-    const uint32_t SBO = 16u * (uint32_t)P, LBO = 128u;
+    constexpr uint32_t SBO = 16u * P, LBO = 128u;
     const int ntiles = (int)((Nc + 127) / 128);
-    const float sc = p.scale, isc = p.inv_scale;
+    float sa = 1.f;
+    if (FP16 && p.amax) {
+        // A entries are sums of at most 1.5 max|X|; scale so that they stay below 2^14
+        int e;
+        float mx = *p.amax;
+        if (mx > 0.f && isfinite(mx)) {
+            frexpf(mx, &e);  // mx < 2^e
+            sa = ldexpf(1.f, 14 - e);
+        }
+    }
+    const float unscale = 1.f / (sa * p.wscale);
     uint32_t phase = 0;
 
-    auto slot_value = [&](int s, int64_t jc, uint32_t cm, int64_t ir) -> float {
-        float v = 0.f;
-        if (s < NS) {
-            const int rm = rowmap[s];
-            if (rm >= 0) {
-                float xv = __ldg(p.X + (int64_t)(rm >> 1) * Nc + jc);
-                v = (rm & 1) ? -xv : xv;
-            }
-            const uint16_t tg = __ldg(p.tslot + (int64_t)s * Nc + jc);
-            if (tg != 0xFFFFu) {
-                float xv = 0.5f * xrow[tg];
-                v += (__popc(cm & betw[s]) & 1) ? -xv : xv;
-            }
-        } else if (s == NS) {
-            v = xrow[jc];
-        }
-        return v * sc;
-    };
-
-    auto build = [&](int t, int buf, int64_t ir) {
+    // Slots are handled in batches of SB: all global loads of a batch are issued
+    // before any of them is used (they are independent), then the values are
+    // combined, split and stored to tensor memory 8 slots (4 columns) at a time.
+    constexpr int SB = 24;
+    auto build = [&](int t, int buf) {
         const int64_t jc = (int64_t)t * 128 + m;
         const bool valid = jc < Nc;
-        const uint32_t cm = valid ? __ldg(p.cmask + jc) : 0u;
+        const int64_t jcc = valid ? jc : Nc - 1;  // clamped address for the tail tile
+        const uint32_t cm = __ldg(p.cmask + jcc);
         const uint32_t a_hi = tbase + lane_base + (uint32_t)(buf * P);
         const uint32_t a_lo = a_hi + (uint32_t)(P / 2);
-        for (int c0 = slot0; c0 < slot1; c0 += 8) {
-            float v[8];
+        const float xself = xrow[jcc];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = valid ? slot_value(c0 + u, jc, cm, ir) : 0.f;
-            uint32_t hi[4], lo[4];
+        for (int b0 = 0; b0 < NH; b0 += SB) {
+            uint32_t tw[SB / 2];
+            float xa[SB];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                float h0 = round16<FP16>(v[2 * u]), h1 = round16<FP16>(v[2 * u + 1]);
-                hi[u] = pack2<FP16>(h0, h1);
-                lo[u] = pack2<FP16>(v[2 * u] - h0, v[2 * u + 1] - h1);
+            for (int i = 0; i < SB; i += 2) {
+                if (b0 + i < NH) {
+                    const int s = slot0 + b0 + i;
+                    tw[i / 2] = __ldg(p.tslot2 + (int64_t)(s >> 1) * Nc + jcc);
+                }
             }
-            tmem_st4(a_hi + (uint32_t)(c0 / 2), hi[0], hi[1], hi[2], hi[3]);
-            tmem_st4(a_lo + (uint32_t)(c0 / 2), lo[0], lo[1], lo[2], lo[3]);
+#pragma unroll
+            for (int i = 0; i < SB; ++i) {
+                if (b0 + i < NH) {
+                    const int rm = rowmap[slot0 + b0 + i];
+                    xa[i] = (rm >= 0) ? __ldg(p.X + (int64_t)(rm >> 1) * Nc + jcc) : 0.f;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < SB; c += 8) {
+                if (b0 + c < NH) {
+                    uint32_t hi[4], lo[4];
+#pragma unroll
+                    for (int u = 0; u < 8; u += 2) {
+                        float v[2];
+#pragma unroll
+                        for (int w = 0; w < 2; ++w) {
+                            const int i = c + u + w;
+                            const int s = slot0 + b0 + i;
+                            const int rm = rowmap[s];
+                            float val = (rm & 1) ? -xa[i] : xa[i];
+                            const uint32_t tg = (tw[i / 2] >> (16 * (i & 1))) & 0xFFFFu;
+                            if (s < NS && tg != 0xFFFFu) {
+                                float xb = 0.5f * xrow[tg];
+                                val += (__popc(cm & betw[s]) & 1) ? -xb : xb;
+                            }
+                            if (s == NS) val = xself;
+                            v[w] = valid ? val * sa : 0.f;
+                        }
+                        const float h0 = round16<FP16>(v[0]), h1 = round16<FP16>(v[1]);
+                        hi[u / 2] = pack2<FP16>(h0, h1);
+                        lo[u / 2] = pack2<FP16>(v[0] - h0, v[1] - h1);
+                    }
+                    const uint32_t col = (uint32_t)((slot0 + b0 + c) / 2);
+                    tmem_st4(a_hi + col, hi[0], hi[1], hi[2], hi[3]);
+                    tmem_st4(a_lo + col, lo[0], lo[1], lo[2], lo[3]);
+                }
+            }
         }
     };
 
@@ -284,10 +323,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_rowpass(const RowPass p) {
         const uint32_t a_hi = tbase + (uint32_t)(buf * P);
         const uint32_t a_lo = a_hi + (uint32_t)(P / 2);
         const uint32_t d = tbase + (uint32_t)(2 * P);
-        const int ksteps = P / 16;
-        for (int pass = 0; pass < 3; ++pass) {
+        constexpr int ksteps = P / 16;
+#pragma unroll
+        for (int pass = 0; pass < NW + 1; ++pass) {
+            // pass 0: A_hi W_0, pass 1: A_lo W_0, pass j+1 (j >= 1): A_hi W_j
             const uint32_t a = (pass == 1) ? a_lo : a_hi;
-            const uint32_t bbase = sB_addr + (pass == 2 ? (uint32_t)(2 * P * P) : 0u);
+            const int piece = pass <= 1 ? 0 : pass - 1;
+            const uint32_t bbase = sB_addr + (uint32_t)(piece * 2 * P * P);
+#pragma unroll
             for (int j = 0; j < ksteps; ++j) {
                 uint64_t bd = smem_desc(bbase + (uint32_t)(j * 256), LBO, SBO);
                 mma_ts(d, a + (uint32_t)(j * 8), bd, idesc, (pass | j) != 0);
@@ -299,20 +342,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_rowpass(const RowPass p) {
     auto epilogue = [&](int t) {
         const int64_t jc = (int64_t)t * 128 + m;
         const bool valid = jc < Nc;
-        const uint32_t cm = valid ? __ldg(p.cmask + jc) : 0u;
-        const uint32_t dcol = tbase + lane_base + (uint32_t)(2 * P);
-        for (int c0 = slot0; c0 < slot1; c0 += 8) {
-            uint32_t r[8];
-            tmem_ld8(dcol + (uint32_t)c0, r);
-            tmem_ld_wait();
-            if (valid) {
+        const int64_t jcc = valid ? jc : Nc - 1;
+        const uint32_t cm = __ldg(p.cmask + jcc);
+        const uint32_t dcol = tbase + lane_base + (uint32_t)(2 * P + slot0);
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int s = c0 + u;
-                    if (s < NS) {
-                        const uint16_t tg = __ldg(p.tslot + (int64_t)s * Nc + jc);
-                        if (tg != 0xFFFFu) {
-                            float g = __uint_as_float(r[u]) * isc;
+        for (int b0 = 0; b0 < NH; b0 += SB) {
+            uint32_t tw[SB / 2];
+#pragma unroll
+            for (int i = 0; i < SB; i += 2)
+                if (b0 + i < NH)
+                    tw[i / 2] = __ldg(p.tslot2 + (int64_t)((slot0 + b0 + i) >> 1) * Nc + jcc);
+#pragma unroll
+            for (int c = 0; c < SB; c += 8) {
+                if (b0 + c < NH) {
+                    uint32_t r[8];
+                    tmem_ld8(dcol + (uint32_t)(b0 + c), r);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int i = c + u;
+                        const int s = slot0 + b0 + i;
+                        const uint32_t tg = (tw[i / 2] >> (16 * (i & 1))) & 0xFFFFu;
+                        if (valid && s < NS && tg != 0xFFFFu) {
+                            float g = __uint_as_float(r[u]) * unscale;
                             if (__popc(cm & betw[s]) & 1) g = -g;
                             atomicAdd(srow + tg, g);
                         }
@@ -338,7 +390,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_rowpass(const RowPass p) {
         }
         __syncthreads();
 
-        build(0, 0, ir);
+        build(0, 0);
         tmem_st_wait();
         tc_fence_before();
         __syncthreads();
@@ -347,7 +399,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_rowpass(const RowPass p) {
             issue(0);
         }
         for (int t = 0; t < ntiles; ++t) {
-            if (t + 1 < ntiles) build(t + 1, (t + 1) & 1, ir);
+            if (t + 1 < ntiles) build(t + 1, (t + 1) & 1);
             if (tid == 0) {
                 long long t0 = clock64();
                 while (!mbar_try_wait(mbar, phase)) {
@@ -381,14 +433,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_rowpass(const RowPass p) {
     if (warp == 0) tmem_dealloc(tbase, p.ncols);
 }
 
+// max |x| as float bits (non-negative floats order like unsigned integers)
+__global__ void k_absmax(const float* __restrict__ x, int64_t n, unsigned* out) {
+    float mx = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        mx = fmaxf(mx, fabsf(x[i]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(mx));
+}
+
 // ---------------------------------------------------------------- set-up kernels
 
 // W image: B operand of the MMA is W^T (N = output slot, K = input slot) in the
 // canonical K-major layout; element (nr, kc) at (nr/8)*16P + (kc/8)*128 +
-// (nr%8)*16 + (kc%8)*2 bytes.  hi = round(W), lo = round(W - hi).
+// (nr%8)*16 + (kc%8)*2 bytes.  W (scaled by the power of two wscale) is split
+// into NW 16-bit pieces, piece j = round(W - sum_{i<j} piece_i); piece j sits at
+// byte offset j * 2 P^2.
 template <bool FP16>
 __global__ void k_wimg(const double* __restrict__ h1, const double* __restrict__ eri, int n,
-                       int P, int NS, uint8_t* __restrict__ img, double wscale) {
+                       int P, int NS, int NW, uint8_t* __restrict__ img, double wscale) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= P * P) return;
     const int nr = idx / P;  // output slot
@@ -408,29 +472,28 @@ __global__ void k_wimg(const double* __restrict__ h1, const double* __restrict__
         }
     }
     w *= wscale;
-    float hi_f, lo_f;
-    uint16_t hb, lb;
-    if (FP16) {
-        __half h = __double2half(w);
-        hi_f = __half2float(h);
-        __half l = __double2half(w - (double)hi_f);
-        hb = *reinterpret_cast<uint16_t*>(&h);
-        lb = *reinterpret_cast<uint16_t*>(&l);
-    } else {
-        __nv_bfloat16 h = __double2bfloat16(w);
-        hi_f = __bfloat162float(h);
-        __nv_bfloat16 l = __double2bfloat16(w - (double)hi_f);
-        hb = *reinterpret_cast<uint16_t*>(&h);
-        lb = *reinterpret_cast<uint16_t*>(&l);
-    }
-    (void)lo_f;
     const size_t off = (size_t)(nr / 8) * (16 * P) + (size_t)(kc / 8) * 128 + (nr % 8) * 16 +
                        (kc % 8) * 2;
-    *reinterpret_cast<uint16_t*>(img + off) = hb;
-    *reinterpret_cast<uint16_t*>(img + 2 * (size_t)P * P + off) = lb;
+    double rest = w;
+    for (int j = 0; j < NW; ++j) {
+        uint16_t bits;
+        double part;
+        if (FP16) {
+            __half h = __double2half(rest);
+            part = (double)__half2float(h);
+            bits = *reinterpret_cast<uint16_t*>(&h);
+        } else {
+            __nv_bfloat16 h = __double2bfloat16(rest);
+            part = (double)__bfloat162float(h);
+            bits = *reinterpret_cast<uint16_t*>(&h);
+        }
+        *reinterpret_cast<uint16_t*>(img + (size_t)j * 2 * P * P + off) = bits;
+        rest -= part;
+    }
 }
 
-// slot table: for string j and its entry (pq -> tgt), slot {p,q} -> tgt.
+// slot table: for string j and its entry (pq -> tgt), slot s = {p,q} -> tgt, stored
+// as 16-bit pairs: word (s/2, j) holds slots 2*(s/2) (low half) and 2*(s/2)+1.
 __global__ void k_slot_table(const int32_t* __restrict__ tgt, const uint16_t* __restrict__ pq,
                              int64_t ns, int nexc, int n, uint16_t* __restrict__ tslot) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -439,7 +502,7 @@ __global__ void k_slot_table(const int32_t* __restrict__ tgt, const uint16_t* __
     int a = pq[i] / n, b = pq[i] % n;
     if (a > b) { int t = a; a = b; b = t; }
     const int s = b * (b + 1) / 2 + a;
-    tslot[(int64_t)s * ns + j] = (uint16_t)tgt[i];
+    tslot[((int64_t)(s >> 1) * ns + j) * 2 + (s & 1)] = (uint16_t)tgt[i];
 }
 
 // out[c][r] = in[r][c] for an R x C matrix.
@@ -480,14 +543,34 @@ uint32_t tmem_cols(int P) {
     return c;
 }
 
-size_t rowpass_smem(int P, int64_t Nc) {
-    return (size_t)4 * P * P + 8 * (size_t)Nc + 8 * (size_t)P + 64;
+size_t rowpass_smem(int P, int NW, int64_t Nc) {
+    return (size_t)2 * NW * P * P + 8 * (size_t)Nc + 8 * (size_t)P + 64;
+}
+
+template <int P>
+void* rowpass_fn(bool fp16) {
+    return fp16 ? (void*)k_rowpass<P, true, 3> : (void*)k_rowpass<P, false, 2>;
+}
+
+void* rowpass_kernel(int P, bool fp16) {
+    switch (P) {
+        case 16: return rowpass_fn<16>(fp16);
+        case 32: return rowpass_fn<32>(fp16);
+        case 48: return rowpass_fn<48>(fp16);
+        case 64: return rowpass_fn<64>(fp16);
+        case 80: return rowpass_fn<80>(fp16);
+        case 96: return rowpass_fn<96>(fp16);
+        case 112: return rowpass_fn<112>(fp16);
+        case 128: return rowpass_fn<128>(fp16);
+        case 144: return rowpass_fn<144>(fp16);
+        default: return nullptr;
+    }
 }
 
 }  // namespace
 
 void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
-                   const double* d_eri, int norb, cudaStream_t st) {
+                   const double* d_eri, int norb, double wmax, bool use_fp16, cudaStream_t st) {
     ta = &A;
     tb = &B;
     n = norb;
@@ -496,35 +579,44 @@ void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
     nsa = A.ns;
     nsb = B.ns;
     dim = nsa * nsb;
-    fp16 = false;
-    if (tmem_cols(P) > 512)
-        KPM_THROW(KPM_EUNSUPPORTED, "KPM_MIXED supports up to 17 orbitals (tensor memory)");
+    fp16 = use_fp16;
+    nw = fp16 ? 3 : 2;
+    kernel = rowpass_kernel(P, fp16);
+    if (!kernel || tmem_cols(P) > 512)
+        KPM_THROW(KPM_EUNSUPPORTED, "tensor-core sigma supports up to 16 orbitals");
     int dev = 0;
     KPM_CUDA(cudaGetDevice(&dev));
     cudaDeviceProp prop;
     KPM_CUDA(cudaGetDeviceProperties(&prop, dev));
     if (prop.major != 10)
-        KPM_THROW(KPM_EUNSUPPORTED, "KPM_MIXED needs a Blackwell (sm_10x) GPU");
+        KPM_THROW(KPM_EUNSUPPORTED, "tensor-core sigma needs a Blackwell (sm_10x) GPU");
     nsm = prop.multiProcessorCount;
     int64_t ncmax = nsa > nsb ? nsa : nsb;
-    smem_bytes = rowpass_smem(P, ncmax);
+    smem_bytes = rowpass_smem(P, nw, ncmax);
     // at least ~116 KB so that exactly one CTA (and one TMEM allocation) fits per SM
     size_t floor_bytes = 116 * 1024;
     if (smem_bytes < floor_bytes) smem_bytes = floor_bytes;
     if (smem_bytes > (size_t)prop.sharedMemPerBlockOptin)
-        KPM_THROW(KPM_EUNSUPPORTED, "KPM_MIXED: row of %lld strings needs %zu B shared memory",
+        KPM_THROW(KPM_EUNSUPPORTED, "tensor-core sigma: rows of %lld strings need %zu B of shared memory",
                   (long long)ncmax, smem_bytes);
-    KPM_CUDA(cudaFuncSetAttribute(k_rowpass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    KPM_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem_bytes));
-    KPM_CUDA(cudaFuncSetAttribute(k_rowpass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem_bytes));
-
-    wimg.alloc((size_t)4 * P * P);
-    KPM_CUDA(cudaMemsetAsync(wimg.p, 0, (size_t)4 * P * P, st));
+    // W scaled by a power of two so that |W| < 2^14 (FP16 range); BF16 needs none
+    wscale = 1.0f;
+    if (fp16 && wmax > 0.0) {
+        int e;
+        std::frexp(wmax, &e);
+        wscale = std::ldexp(1.0f, 14 - e);
+    }
+    size_t wbytes = (size_t)2 * nw * P * P;
+    wimg.alloc(wbytes);
+    KPM_CUDA(cudaMemsetAsync(wimg.p, 0, wbytes, st));
     if (fp16)
-        k_wimg<true><<<(P * P + 255) / 256, 256, 0, st>>>(d_h1, d_eri, n, P, NS, wimg.as<uint8_t>(), 1.0);
+        k_wimg<true><<<(P * P + 255) / 256, 256, 0, st>>>(d_h1, d_eri, n, P, NS, nw,
+                                                          wimg.as<uint8_t>(), (double)wscale);
     else
-        k_wimg<false><<<(P * P + 255) / 256, 256, 0, st>>>(d_h1, d_eri, n, P, NS, wimg.as<uint8_t>(), 1.0);
+        k_wimg<false><<<(P * P + 255) / 256, 256, 0, st>>>(d_h1, d_eri, n, P, NS, nw,
+                                                           wimg.as<uint8_t>(), (double)wscale);
     KPM_LAUNCHED();
 
     auto build_slots = [&](const SpinTables& T, DevBuf& out) {
@@ -543,6 +635,7 @@ void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
     xt.alloc((size_t)dim * sizeof(float));
     sp.alloc((size_t)dim * sizeof(float));
     err.alloc(sizeof(int));
+    amax.alloc(2 * sizeof(unsigned));
     KPM_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
 }
 
@@ -551,25 +644,33 @@ void TcSigma::apply(const float* x, float* y, int ncol, cudaStream_t st) {
     for (int c = 0; c < ncol; ++c) {
         const float* X = x + (size_t)c * dim;
         float* Y = y + (size_t)c * dim;
+        const float* am = nullptr;
+        if (fp16) {
+            // both passes read the same numbers (x and its transpose)
+            KPM_CUDA(cudaMemsetAsync(amax.p, 0, sizeof(unsigned), st));
+            k_absmax<<<1024, 256, 0, st>>>(X, dim, amax.as<unsigned>());
+            KPM_LAUNCHED();
+            am = reinterpret_cast<const float*>(amax.p);
+        }
         // pass 1: rows alpha, columns beta, opposite-spin part on
-        RowPass p1{X, Y, nsa, nsb, slot_b.as<uint16_t>(), tb->masks.as<uint32_t>(),
+        RowPass p1{X, Y, nsa, nsb, slot_b.as<uint32_t>(), tb->masks.as<uint32_t>(),
                    ta->tgt.as<int32_t>(), ta->pq.as<uint16_t>(), ta->sgn.as<int8_t>(), ta->nexc,
-                   wimg.as<uint4>(), P, NS, n, nc, 1.0f, 1.0f, err.as<int>()};
+                   wimg.as<uint4>(), NS, n, nc, am, wscale, err.as<int>()};
         int g1 = (int)(nsa < nsm ? nsa : nsm);
-        if (fp16) k_rowpass<true><<<g1, TC_THREADS, smem_bytes, st>>>(p1);
-        else k_rowpass<false><<<g1, TC_THREADS, smem_bytes, st>>>(p1);
+        void* args1[] = {&p1};
+        KPM_CUDA(cudaLaunchKernel(kernel, dim3(g1), dim3(TC_THREADS), args1, smem_bytes, st));
         KPM_LAUNCHED();
         // pass 2 on x^T: rows beta, columns alpha, same-spin alpha part only
         dim3 tb2(32, 8);
         dim3 gt((unsigned)((nsb + 31) / 32), (unsigned)((nsa + 31) / 32));
         k_transpose<<<gt, tb2, 0, st>>>(X, xt.as<float>(), nsa, nsb);
         KPM_LAUNCHED();
-        RowPass p2{xt.as<float>(), sp.as<float>(), nsb, nsa, slot_a.as<uint16_t>(),
-                   ta->masks.as<uint32_t>(), nullptr, nullptr, nullptr, 0, wimg.as<uint4>(), P,
-                   NS, n, nc, 1.0f, 1.0f, err.as<int>()};
+        RowPass p2{xt.as<float>(), sp.as<float>(), nsb, nsa, slot_a.as<uint32_t>(),
+                   ta->masks.as<uint32_t>(), nullptr, nullptr, nullptr, 0, wimg.as<uint4>(),
+                   NS, n, nc, am, wscale, err.as<int>()};
         int g2 = (int)(nsb < nsm ? nsb : nsm);
-        if (fp16) k_rowpass<true><<<g2, TC_THREADS, smem_bytes, st>>>(p2);
-        else k_rowpass<false><<<g2, TC_THREADS, smem_bytes, st>>>(p2);
+        void* args2[] = {&p2};
+        KPM_CUDA(cudaLaunchKernel(kernel, dim3(g2), dim3(TC_THREADS), args2, smem_bytes, st));
         KPM_LAUNCHED();
         k_add_transposed<<<gt, tb2, 0, st>>>(Y, sp.as<float>(), nsa, nsb);
         KPM_LAUNCHED();
