@@ -55,6 +55,8 @@ def parse_args():
     p.add_argument("--e2e-requests", type=int, default=2)
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--sigma-only", type=int, default=0,
+                   help="time this many H applications (kpm_sigma) and exit; for profiling")
     return p.parse_args()
 
 
@@ -372,8 +374,36 @@ def run_reference(args, ws, rank, pg):
     }
 
 
+def run_sigma_only(args):
+    """K applications of H on one column (no recursion); prints one JSON line."""
+    import torch
+
+    from paper_2506_07430_gb300 import KPM
+    w = synthetic.workload(args.workload)
+    n, na, nb = w["norb"], w["nalpha"], w["nbeta"]
+    I = synthetic.integrals(n, na, nb, w["seed"])
+    k = KPM(I.h1, I.eri, I.dipole, n, na, nb, precision=args.precision)
+    x = torch.from_numpy(synthetic.random_state(k.dim, 7)).to(k.vdtype).cuda()
+    y = torch.empty_like(x)
+    k.sigma(x, y)
+    k.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.sigma_only):
+        k.sigma(x, y)
+    e1.record()
+    k.synchronize()
+    ms = e0.elapsed_time(e1) / args.sigma_only
+    print(json.dumps({"mode": "sigma-only", "workload": args.workload, "precision": args.precision,
+                      "dim": k.dim, "ms_per_sigma": ms}), flush=True)
+    k.close()
+
+
 def main():
     args = parse_args()
+    if args.sigma_only:
+        run_sigma_only(args)
+        return
     if args.impl == "reference":
         # rank 0 alone times the oracle; other ranks exit without work
         ws = int(os.environ.get("WORLD_SIZE", "1"))
