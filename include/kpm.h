@@ -222,6 +222,34 @@ kpm_status kpm_synchronize(kpm_ctx* ctx);
 kpm_status kpm_profile_enable(kpm_ctx* ctx, int enable);
 kpm_status kpm_profile_read(kpm_ctx* ctx, double* sigma_ms, int* count);
 
+/*
+ * kpm_spectrum_static -- kpm_spectrum for callers that cannot allocate device
+ * memory.  The paper has no counterpart; this entry point exists for callers
+ * that cannot call cudaMalloc: processes whose device memory is entirely
+ * reserved by another allocator (a framework's caching pool, a fixed memory
+ * plan), where cudaMalloc fails, and latency-critical loops that cannot pay for
+ * cudaMalloc/cudaFree, which synchronise the device.
+ *   moments_dev   [nmoments] FP64 device array (caller-owned).
+ *   omega_dev, intensity_dev  [npoints] FP64 device arrays (caller-owned),
+ *                 filled as kpm_spectrum fills its host outputs.
+ *   cuda_stream   cudaStream_t the two kernels are queued on (asynchronous).
+ * It allocates nothing: its scratch (the damped moments) is a fixed array of
+ * KPM_SPECTRUM_STATIC_MAX_MOMENTS doubles (2 MiB) in the library's device
+ * memory, held by every GPU that loads the library until the process exits.
+ * nmoments above that limit is rejected with KPM_EINVAL.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) and caches
+ * it; make that first call before any stream capture.  Every call on a device
+ * shares the one array, so calls whose work overlaps on the GPU (for example
+ * on two streams at once) race and give undefined results; serialise them.
+ * The array needs no clearing: every element read is written first in stream
+ * order.  Errors: KPM_EINVAL (arguments, size), KPM_ECUDA; message via
+ * kpm_last_error(NULL).
+ */
+#define KPM_SPECTRUM_STATIC_MAX_MOMENTS 262144
+kpm_status kpm_spectrum_static(const double* moments_dev, int nmoments, double a, double b,
+                               int npoints, int kernel, double* omega_dev,
+                               double* intensity_dev, void* cuda_stream);
+
 /* Number of kernels this library launched on the calling process so far. */
 uint64_t kpm_launch_count(void);
 

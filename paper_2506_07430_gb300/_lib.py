@@ -40,6 +40,7 @@ SIGNATURES = {
     "kpm_synchronize": (_I, [_P]),
     "kpm_profile_enable": (_I, [_P, _I]),
     "kpm_profile_read": (_I, [_P, _P, _P]),
+    "kpm_spectrum_static": (_I, [_P, _I, _D, _D, _I, _I, _P, _P, _P]),
     "kpm_launch_count": (_U64, []),
 }
 

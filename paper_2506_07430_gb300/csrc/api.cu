@@ -12,6 +12,10 @@ using namespace kpm;
 
 static thread_local std::string g_err = "no error";
 
+namespace kpm {
+void set_thread_error(const std::string& msg) { g_err = msg; }
+}  // namespace kpm
+
 struct kpm_ctx {
     int n = 0, na = 0, nb = 0;
     kpm_precision prec = KPM_FP64;

@@ -36,6 +36,9 @@ struct Error {
                       cudaGetErrorString(_e));                                   \
     } while (0)
 
+// Message returned by kpm_last_error(NULL) on the calling thread.
+void set_thread_error(const std::string& msg);
+
 // Every kernel launch of the library goes through this counter.
 extern std::atomic<uint64_t> g_launches;
 
