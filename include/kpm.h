@@ -250,6 +250,68 @@ kpm_status kpm_spectrum_static(const double* moments_dev, int nmoments, double a
                                int npoints, int kernel, double* omega_dev,
                                double* intensity_dev, void* cuda_stream);
 
+/* ------------------------------------------------------------------ serving
+ *
+ * Continuous batching of spectrum requests on one GPU (this library's
+ * serving layer; the paper computes one spectrum at a time).  A worker thread
+ * admits queued requests (FIFO) when a slot is free and the request's
+ * estimated device memory fits in mem_budget_bytes, keeps every admitted
+ * request's recursion resident on its own stream, advances all resident
+ * requests by steps_per_round Chebyshev steps per round (queued for all of them
+ * before waiting on any, so their kernels overlap), and on completion
+ * reconstructs the spectrum (Jackson kernel optional) of the moments summed
+ * over the requested dipole components and frees the request's memory.
+ * A request computes with the same kernels whether it runs alone or beside
+ * others, so its result is the same.
+ */
+typedef struct kpm_server kpm_server;
+
+typedef struct {
+    size_t mem_budget_bytes; /* device memory admitted requests may hold together     */
+    int max_slots;           /* requests resident at once (>= 1)                      */
+    int steps_per_round;     /* Chebyshev steps per resident request per round (>= 1) */
+    kpm_precision precision; /* arithmetic of every request                           */
+} kpm_server_config;
+
+typedef struct {
+    const double* h1;      /* host [norb*norb], copied at submit                   */
+    const double* eri;     /* host [norb^4], chemist (pq|rs), copied               */
+    const double* dipole;  /* host [3*norb*norb], copied                           */
+    int norb, nalpha, nbeta;
+    const double* psi0;    /* host [dim] ground state, copied                       */
+    unsigned comp_mask;    /* dipole components (bit c = component c)            */
+    double a, b;           /* rescaling H~ = (H - b)/a (e.g. from kpm_bounds)      */
+    int nmoments;          /* even, >= 2                                           */
+    int npoints;           /* Chebyshev nodes of the spectrum                      */
+    int kernel;            /* 1 = Jackson, 0 = none                                */
+} kpm_request;
+
+typedef struct {
+    double* moments;   /* [ncomp][nmoments] or NULL (caller-owned host memory)    */
+    double* omega;     /* [npoints] or NULL, ascending                            */
+    double* intensity; /* [npoints] or NULL, summed over components, per energy   */
+    double t_queue_s;  /* submit -> admission (out)                               */
+    double t_run_s;    /* admission -> result (out)                               */
+    double t_total_s;  /* submit -> result, the request's latency (out)            */
+} kpm_result;
+
+/* Starts the worker thread on the current device.  KPM_EINVAL for a bad
+ * configuration, KPM_ECUDA without a device. */
+kpm_status kpm_server_create(const kpm_server_config* cfg, kpm_server** out);
+/* Queues a request (inputs copied); *id identifies it.  KPM_ENOMEM if it can
+ * never fit the budget, KPM_EINVAL for bad arguments. */
+kpm_status kpm_server_submit(kpm_server* s, const kpm_request* req, uint64_t* id);
+/* Waits up to timeout_ms for request id and copies its results (then forgets
+ * it).  KPM_ETIMEOUT if not finished yet (it stays queued/resident), else the
+ * request's own status (KPM_EBOUNDS, KPM_ECANCELLED, ...). */
+kpm_status kpm_server_wait(kpm_server* s, uint64_t id, int timeout_ms, kpm_result* out);
+/* Cancels a queued or resident request; its wait returns KPM_ECANCELLED. */
+kpm_status kpm_server_cancel(kpm_server* s, uint64_t id);
+/* Device memory held by admitted requests, resident and queued counts. */
+kpm_status kpm_server_stats(kpm_server* s, size_t* mem_used, int* resident, int* queued);
+/* Cancels what is queued, finishes nothing further, joins the worker. */
+void kpm_server_destroy(kpm_server* s);
+
 /* Number of kernels this library launched on the calling process so far. */
 uint64_t kpm_launch_count(void);
 

@@ -70,6 +70,10 @@ def _lib():
             lib.sc_dipole_rows.restype = None
             lib.sc_dipole_rows.argtypes = [P, P, P, I64, P, P]
             lib.sc_omp_threads.restype = ctypes.c_int
+            lib.sc_sigma_rows_hash.restype = None
+            lib.sc_sigma_rows_hash.argtypes = [P, P, I64, P]
+            lib.sc_hashvec.restype = ctypes.c_double
+            lib.sc_hashvec.argtypes = [I64]
             _LIB = lib
     return _LIB
 
@@ -88,6 +92,15 @@ class _CSys(ctypes.Structure):
 
 def _ptr(a: np.ndarray) -> int:
     return a.ctypes.data
+
+
+def hash_vector(idx) -> np.ndarray:
+    """x(i) = ((((i * 0x9E3779B97F4A7C15) >> 48) & 0xFFFF) - 32768) * 2^-24, 64-bit
+    wrap-around multiply; exactly representable in FP32 and FP64."""
+    i = np.asarray(idx, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        h = (i * np.uint64(0x9E3779B97F4A7C15)) >> np.uint64(48)
+    return ((h & np.uint64(0xFFFF)).astype(np.int64) - 32768).astype(np.float64) / 16777216.0
 
 
 class SlaterCondon:
@@ -126,6 +139,13 @@ class SlaterCondon:
         assert x.shape == (self.dim,)
         y = np.empty(len(rows), np.float64)
         _lib().sc_sigma_rows(self._cp(), _ptr(rows), len(rows), _ptr(x), _ptr(y))
+        return y
+
+    def sigma_rows_hash(self, rows):
+        """Rows of H x for the hash test vector x(i) (see ``hash_vector``)."""
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        y = np.empty(len(rows), np.float64)
+        _lib().sc_sigma_rows_hash(self._cp(), _ptr(rows), len(rows), _ptr(y))
         return y
 
     def sigma(self, x):

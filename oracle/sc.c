@@ -171,6 +171,36 @@ void sc_sigma_rows(const sc_system* S, const int64_t* rows, int64_t nrows,
     }
 }
 
+/* Test vector defined by an integer hash of the index, exactly representable in
+ * FP32 and FP64: x(i) = ((((i * 0x9E3779B97F4A7C15) >> 48) & 0xFFFF) - 32768) * 2^-24
+ * (64-bit wrap-around multiply).  Lets huge vectors be checked on sampled rows
+ * without storing x on the host. */
+static inline double hashvec(uint64_t i) {
+    uint64_t h = (i * 0x9E3779B97F4A7C15ull) >> 48;
+    return ((double)(int64_t)(h & 0xFFFFu) - 32768.0) * (1.0 / 16777216.0);
+}
+
+double sc_hashvec(int64_t i) { return hashvec((uint64_t)i); }
+
+/* y[r] = sum_c H[rows[r], c] x(c) with x the hash vector above. */
+void sc_sigma_rows_hash(const sc_system* S, const int64_t* rows, int64_t nrows, double* y) {
+    int64_t cap = sc_row_capacity(S);
+#pragma omp parallel
+    {
+        int64_t* cols = (int64_t*)malloc(sizeof(int64_t) * cap);
+        double* vals = (double*)malloc(sizeof(double) * cap);
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t r = 0; r < nrows; ++r) {
+            int64_t k = sc_row(S, rows[r], cols, vals);
+            double acc = 0.0;
+            for (int64_t t = 0; t < k; ++t) acc += vals[t] * hashvec((uint64_t)cols[t]);
+            y[r] = acc;
+        }
+        free(cols);
+        free(vals);
+    }
+}
+
 /* Full y = H x. */
 void sc_sigma(const sc_system* S, const double* x, double* y) {
     int64_t dim = S->nsa * S->nsb;

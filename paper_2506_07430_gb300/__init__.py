@@ -11,11 +11,12 @@ from ._lib import (  # noqa: F401
     KPM,
     KPMError,
     PRECISIONS,
+    Server,
     launch_count,
     library_path,
     load_library,
     spectrum,
 )
 
-__all__ = ["KPM", "KPMError", "PRECISIONS", "spectrum", "launch_count", "load_library",
+__all__ = ["KPM", "KPMError", "PRECISIONS", "Server", "spectrum", "launch_count", "load_library",
            "library_path"]

@@ -41,8 +41,30 @@ SIGNATURES = {
     "kpm_profile_enable": (_I, [_P, _I]),
     "kpm_profile_read": (_I, [_P, _P, _P]),
     "kpm_spectrum_static": (_I, [_P, _I, _D, _D, _I, _I, _P, _P, _P]),
+    "kpm_server_create": (_I, [_P, _P]),
+    "kpm_server_submit": (_I, [_P, _P, _P]),
+    "kpm_server_wait": (_I, [_P, _U64, _I, _P]),
+    "kpm_server_cancel": (_I, [_P, _U64]),
+    "kpm_server_stats": (_I, [_P, _P, _P, _P]),
+    "kpm_server_destroy": (None, [_P]),
     "kpm_launch_count": (_U64, []),
 }
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int),
+                ("steps_per_round", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("h1", _P), ("eri", _P), ("dipole", _P), ("norb", _I), ("nalpha", _I),
+                ("nbeta", _I), ("psi0", _P), ("comp_mask", _U), ("a", _D), ("b", _D),
+                ("nmoments", _I), ("npoints", _I), ("kernel", _I)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("moments", _P), ("omega", _P), ("intensity", _P), ("t_queue_s", _D),
+                ("t_run_s", _D), ("t_total_s", _D)]
 
 
 class KPMError(RuntimeError):
@@ -233,6 +255,69 @@ class KPM:
             _check(st, self._h)
         k = nm.value
         return out.reshape(-1)[: self._rec_ncomp * k].reshape(self._rec_ncomp, k)
+
+
+class Server:
+    """Continuous-batching spectrum server (kpm_server_*)."""
+
+    def __init__(self, mem_budget_bytes: int, max_slots: int = 8, steps_per_round: int = 16,
+                 precision: str = "mixed"):
+        lib = load_library()
+        cfg = ServerConfig(int(mem_budget_bytes), int(max_slots), int(steps_per_round),
+                           PRECISIONS[precision])
+        h = ctypes.c_void_p()
+        _check(lib.kpm_server_create(ctypes.byref(cfg), ctypes.byref(h)), None)
+        self._h = h
+        self._pending = {}
+
+    def submit(self, h1, eri, dipole, norb, nalpha, nbeta, psi0, comp_mask, a, b, nmoments,
+               npoints=2048, kernel="jackson"):
+        keep = [np.ascontiguousarray(h1, dtype=np.float64),
+                np.ascontiguousarray(eri, dtype=np.float64),
+                np.ascontiguousarray(dipole, dtype=np.float64),
+                np.ascontiguousarray(psi0, dtype=np.float64)]
+        r = Request(_np_ptr(keep[0]), _np_ptr(keep[1]), _np_ptr(keep[2]), norb, nalpha, nbeta,
+                    _np_ptr(keep[3]), comp_mask, a, b, nmoments, npoints,
+                    1 if kernel == "jackson" else 0)
+        rid = ctypes.c_uint64()
+        _check(load_library().kpm_server_submit(self._h, ctypes.byref(r), ctypes.byref(rid)), None)
+        self._pending[rid.value] = (bin(comp_mask).count("1"), nmoments, npoints)
+        return rid.value
+
+    def wait(self, rid: int, timeout_ms: int = 600000, allow_ebounds: bool = False):
+        ncomp, nm, npts = self._pending[rid]
+        mom = np.zeros((ncomp, nm))
+        om = np.zeros(npts)
+        it = np.zeros(npts)
+        res = Result(_np_ptr(mom), _np_ptr(om), _np_ptr(it), 0.0, 0.0, 0.0)
+        st = load_library().kpm_server_wait(self._h, rid, timeout_ms, ctypes.byref(res))
+        if st == KPM_ETIMEOUT:
+            _check(st, None)
+        del self._pending[rid]
+        if not (st == KPM_OK or (allow_ebounds and st == KPM_EBOUNDS)):
+            _check(st, None)
+        return {"moments": mom, "omega": om, "intensity": it, "t_queue_s": res.t_queue_s,
+                "t_run_s": res.t_run_s, "t_total_s": res.t_total_s, "status": st}
+
+    def cancel(self, rid: int):
+        _check(load_library().kpm_server_cancel(self._h, rid), None)
+
+    def stats(self):
+        mem, res, q = ctypes.c_size_t(), ctypes.c_int(), ctypes.c_int()
+        _check(load_library().kpm_server_stats(self._h, ctypes.byref(mem), ctypes.byref(res),
+                                               ctypes.byref(q)), None)
+        return {"mem_used": mem.value, "resident": res.value, "queued": q.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().kpm_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def spectrum(moments, a: float, b: float, npoints: int = 2048, kernel: str = "jackson"):

@@ -297,18 +297,29 @@ kpm_status kpm_create(const double* h1, const double* eri, const double* dipole,
             exact_diagonal(c->ta, *c->tb, c->d_eri.as<double>(), norb, c->d_diag.as<float2>(), c->st);
         }
         if (prec == KPM_MIXED || prec == KPM_MIXED_BF16) {
-            double wmax = 0.0;
-            for (int64_t i = 0; i < n4; ++i) wmax = std::fmax(wmax, std::fabs(eri[i]));
-            for (int p = 0; p < norb; ++p)
-                for (int q = 0; q < norb; ++q) {
-                    double k = h1[p * norb + q];
-                    for (int r = 0; r < norb; ++r)
-                        k -= 0.5 * eri[(((int64_t)p * norb + r) * norb + r) * norb + q];
+            // W over unordered pairs {p<=q}: rows (pq|rs) and the one-body row k_pq.
+            // wmax = max |W|, wcol = max over output pairs of the column sum of |W|.
+            double wmax = 0.0, wcol = 0.0;
+            auto eri_at = [&](int p, int q, int r, int s) {
+                return eri[(((int64_t)p * norb + q) * norb + r) * norb + s];
+            };
+            for (int r = 0; r < norb; ++r)
+                for (int s = r; s < norb; ++s) {
+                    double k = h1[r * norb + s];
+                    for (int t = 0; t < norb; ++t) k -= 0.5 * eri_at(r, t, t, s);
+                    double col = std::fabs(k);
                     wmax = std::fmax(wmax, std::fabs(k));
+                    for (int p = 0; p < norb; ++p)
+                        for (int q = p; q < norb; ++q) {
+                            double v = std::fabs(eri_at(p, q, r, s));
+                            col += v;
+                            wmax = std::fmax(wmax, v);
+                        }
+                    wcol = std::fmax(wcol, col);
                 }
             c->tc.reset(new TcSigma());
             c->tc->init(c->ta, *c->tb, c->d_h1.as<double>(), c->d_eri.as<double>(), norb, wmax,
-                        prec == KPM_MIXED, c->st);
+                        wcol, prec == KPM_MIXED, c->st);
         }
         KPM_CUDA(cudaStreamSynchronize(c->st));
     });

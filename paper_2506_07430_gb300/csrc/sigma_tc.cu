@@ -46,7 +46,6 @@ namespace kpm {
 
 namespace {
 
-constexpr int TC_THREADS = 256;
 constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -170,8 +169,9 @@ struct RowPass {
     const float* X;
     float* Y;
     int64_t Nr, Nc;
-    const uint32_t* tslot2;  // [P/2][Nc]: targets of slots 2i (low 16 bits) and 2i+1
-    const uint32_t* cmask;   // [Nc]
+    const uint4* tslot8;     // [P/8][Nc]: 8 16-bit entries per chunk of 8 slots (slot 8c+u in
+                             // half u of the 128-bit word): target string | sign << 15,
+                             // Nc when the slot is absent
     const int32_t* rtgt;     // [Nr][rnexc] row-string tables (opposite-spin part)
     const uint16_t* rpq;
     const int8_t* rsgn;
@@ -179,49 +179,52 @@ struct RowPass {
     const uint4* wimg;       // W image: NW pieces of 2 P^2 bytes each
     int NS, n;
     uint32_t ncols;          // TMEM columns allocated
-    const float* amax;       // device max|X| (FP16 operand scaling), or nullptr
+    const float* amax;       // device max|X| (operand scaling and fixed-point range)
     float wscale;            // power-of-two scale applied to W in the image
+    float gbound;            // max over output slots of sum_k |W[k][s]| (unscaled W)
+    int nexc_c;              // table entries per column string (contributions per target)
     int* err;
 };
+
+constexpr int RP_WARPS = 16;                 // 4 warps per TMEM lane quadrant
+constexpr int RP_THREADS = 32 * RP_WARPS;
 
 // P: padded K = N (multiple of 16); FP16: operand format (else BF16);
 // NW: number of 16-bit pieces of W (2 or 3).  MMA passes: A_hi W_j for every
 // piece j, plus A_lo W_0.
+//
+// Work split: the P slots form P/8 chunks of 8; the 4 warps of a lane quadrant
+// take the chunks round-robin (chunk c -> warp c % 4 of the quadrant).  Per
+// tile t the CTA (i) waits for MMA(t), (ii) copies D(t) into registers, (iii)
+// issues MMA(t+1), (iv) builds A(t+2) into the buffer MMA(t) has finished with,
+// and (v) scatters D(t) from registers; so the tensor core runs while the CUDA
+// cores build and scatter.
 template <int P, bool FP16, int NW>
-__global__ void __launch_bounds__(TC_THREADS, 1) k_rowpass(const RowPass p) {
-    constexpr int NH = P / 2;  // slots per half
+__global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
+    constexpr int NCH = P / 8;                     // 8-slot chunks
+    constexpr int MAXC = (NCH + 3) / 4;            // chunks per warp (upper bound)
     extern __shared__ __align__(1024) unsigned char smem[];
     const int NS = p.NS;
     const int64_t Nc = p.Nc;
     uint8_t* sB = smem;
-    float* xrow = reinterpret_cast<float*>(smem + 2 * NW * P * P);
-    float* srow = xrow + Nc;
-    int32_t* rowmap = reinterpret_cast<int32_t*>(srow + Nc);
-    uint32_t* betw = reinterpret_cast<uint32_t*>(rowmap + P);
-    uintptr_t tail = (reinterpret_cast<uintptr_t>(betw + P) + 15) & ~uintptr_t(15);
+    float* xrow = reinterpret_cast<float*>(smem + 2 * NW * P * P);   // Nc + 1 (zero pad)
+    int* srow = reinterpret_cast<int*>(xrow + (Nc + 1));             // Nc + 1, fixed point
+    float* ma = reinterpret_cast<float*>(srow + (Nc + 1));           // [P] opposite-spin / identity multiplier
+    int32_t* rj = reinterpret_cast<int32_t*>(ma + P);                // [P] source row of that term
+    uintptr_t tail = (reinterpret_cast<uintptr_t>(rj + P) + 15) & ~uintptr_t(15);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(tail);
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(mbar + 1);
     int* abort_flag = reinterpret_cast<int*>(tmem_holder + 1);
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int quad = warp & 3, half = warp >> 2;
+    const int quad = warp & 3, wq = warp >> 2;
     const int m = quad * 32 + lane;
-    const int slot0 = half * NH;
 
     {
         constexpr int nv = (2 * NW * P * P) / 16;
         uint4* dst = reinterpret_cast<uint4*>(sB);
-        for (int i = tid; i < nv; i += TC_THREADS) dst[i] = p.wimg[i];
-    }
-    for (int s = tid; s < P; s += TC_THREADS) {
-        uint32_t bm = 0;
-        if (s < NS) {
-            int a, b;
-            slot_pair(s, a, b);  // a <= b
-            if (a != b) bm = ((1u << b) - 1u) & ~((2u << a) - 1u);
-        }
-        betw[s] = bm;
+        for (int i = tid; i < nv; i += RP_THREADS) dst[i] = p.wimg[i];
     }
     if (tid == 0) {
         mbar_init(mbar, 1);
@@ -242,78 +245,68 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_rowpass(const RowPass p) {
     const uint32_t sB_addr = smem_u32(sB);
     constexpr uint32_t SBO = 16u * P, LBO = 128u;
     const int ntiles = (int)((Nc + 127) / 128);
-    float sa = 1.f;
-    if (FP16 && p.amax) {
-        // A entries are sums of at most 1.5 max|X|; scale so that they stay below 2^14
-        int e;
-        float mx = *p.amax;
+    // Operand scale (FP16): A entries stay below 1.5 * 2^14.  Fixed point for the
+    // scattered sums: every target receives nexc_c terms of magnitude at most
+    // |G| <= 1.5 max|x| gbound, so with fx = 2^f and
+    // fx * 1.02 * nexc_c * 1.5 * max|x| * gbound < 2^31 no partial sum overflows.
+    // Integer addition is associative: the sums do not depend on the order of the
+    // atomics.
+    float sa = 1.f, fx = 1.f;
+    {
+        const float mx = *p.amax;
         if (mx > 0.f && isfinite(mx)) {
+            int e;
             frexpf(mx, &e);  // mx < 2^e
-            sa = ldexpf(1.f, 14 - e);
+            if (FP16) sa = ldexpf(1.f, 14 - max(e, -90));
+            const float bound = 1.02f * (float)p.nexc_c * 1.5f * mx * p.gbound;
+            int f = -90;
+            if (bound > 0.f) frexpf(bound, &f);  // bound < 2^f
+            fx = ldexpf(1.f, 31 - max(f, -90));
         }
     }
-    const float unscale = 1.f / (sa * p.wscale);
+    const float half_sa = 0.5f * sa;
+    const float unscale = fx / (sa * p.wscale);   // D -> fixed point
+    const float inv_fx = 1.f / fx;
+    const uint32_t absent = (uint32_t)Nc;
     uint32_t phase = 0;
 
-    // Slots are handled in batches of SB: all global loads of a batch are issued
-    // before any of them is used (they are independent), then the values are
-    // combined, split and stored to tensor memory 8 slots (4 columns) at a time.
-    constexpr int SB = 24;
     auto build = [&](int t, int buf) {
         const int64_t jc = (int64_t)t * 128 + m;
         const bool valid = jc < Nc;
         const int64_t jcc = valid ? jc : Nc - 1;  // clamped address for the tail tile
-        const uint32_t cm = __ldg(p.cmask + jcc);
         const uint32_t a_hi = tbase + lane_base + (uint32_t)(buf * P);
         const uint32_t a_lo = a_hi + (uint32_t)(P / 2);
-        const float xself = xrow[jcc];
 #pragma unroll
-        for (int b0 = 0; b0 < NH; b0 += SB) {
-            uint32_t tw[SB / 2];
-            float xa[SB];
+        for (int k = 0; k < MAXC; ++k) {
+            const int c = wq + 4 * k;
+            if (c < NCH) {
+                const int s0 = c * 8;
+                const uint4 w4 = __ldg(p.tslot8 + (int64_t)c * Nc + jcc);
+                const uint32_t w[4] = {w4.x, w4.y, w4.z, w4.w};
+                float xa[8];
 #pragma unroll
-            for (int i = 0; i < SB; i += 2) {
-                if (b0 + i < NH) {
-                    const int s = slot0 + b0 + i;
-                    tw[i / 2] = __ldg(p.tslot2 + (int64_t)(s >> 1) * Nc + jcc);
+                for (int u = 0; u < 8; ++u) {
+                    const float mult = ma[s0 + u];
+                    xa[u] = (mult != 0.f) ? mult * __ldg(p.X + (int64_t)rj[s0 + u] * Nc + jcc) : 0.f;
                 }
-            }
+                uint32_t hi[4], lo[4];
 #pragma unroll
-            for (int i = 0; i < SB; ++i) {
-                if (b0 + i < NH) {
-                    const int rm = rowmap[slot0 + b0 + i];
-                    xa[i] = (rm >= 0) ? __ldg(p.X + (int64_t)(rm >> 1) * Nc + jcc) : 0.f;
-                }
-            }
+                for (int u = 0; u < 8; u += 2) {
+                    float v[2];
 #pragma unroll
-            for (int c = 0; c < SB; c += 8) {
-                if (b0 + c < NH) {
-                    uint32_t hi[4], lo[4];
-#pragma unroll
-                    for (int u = 0; u < 8; u += 2) {
-                        float v[2];
-#pragma unroll
-                        for (int w = 0; w < 2; ++w) {
-                            const int i = c + u + w;
-                            const int s = slot0 + b0 + i;
-                            const int rm = rowmap[s];
-                            float val = (rm & 1) ? -xa[i] : xa[i];
-                            const uint32_t tg = (tw[i / 2] >> (16 * (i & 1))) & 0xFFFFu;
-                            if (s < NS && tg != 0xFFFFu) {
-                                float xb = 0.5f * xrow[tg];
-                                val += (__popc(cm & betw[s]) & 1) ? -xb : xb;
-                            }
-                            if (s == NS) val = xself;
-                            v[w] = valid ? val * sa : 0.f;
-                        }
-                        const float h0 = round16<FP16>(v[0]), h1 = round16<FP16>(v[1]);
-                        hi[u / 2] = pack2<FP16>(h0, h1);
-                        lo[u / 2] = pack2<FP16>(v[0] - h0, v[1] - h1);
+                    for (int q = 0; q < 2; ++q) {
+                        const uint32_t e = (w[(u + q) >> 1] >> (16 * ((u + q) & 1))) & 0xFFFFu;
+                        const float xb = xrow[e & 0x7FFFu];
+                        const float sb = __uint_as_float(__float_as_uint(xb) ^ ((e & 0x8000u) << 16));
+                        v[q] = valid ? fmaf(half_sa, sb, xa[u + q]) : 0.f;
                     }
-                    const uint32_t col = (uint32_t)((slot0 + b0 + c) / 2);
-                    tmem_st4(a_hi + col, hi[0], hi[1], hi[2], hi[3]);
-                    tmem_st4(a_lo + col, lo[0], lo[1], lo[2], lo[3]);
+                    const float h0 = round16<FP16>(v[0]), h1 = round16<FP16>(v[1]);
+                    hi[u / 2] = pack2<FP16>(h0, h1);
+                    lo[u / 2] = pack2<FP16>(v[0] - h0, v[1] - h1);
                 }
+                const uint32_t col = (uint32_t)(s0 / 2);
+                tmem_st4(a_hi + col, hi[0], hi[1], hi[2], hi[3]);
+                tmem_st4(a_lo + col, lo[0], lo[1], lo[2], lo[3]);
             }
         }
     };
@@ -339,54 +332,73 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_rowpass(const RowPass p) {
         mma_commit(mbar);
     };
 
-    auto epilogue = [&](int t) {
+    // D(t) of this thread's row and this warp's chunks -> registers
+    auto load_d = [&](uint32_t (&dr)[MAXC][8]) {
+        const uint32_t dcol = tbase + lane_base + (uint32_t)(2 * P);
+#pragma unroll
+        for (int k = 0; k < MAXC; ++k) {
+            const int c = wq + 4 * k;
+            if (c < NCH) tmem_ld8(dcol + (uint32_t)(c * 8), dr[k]);
+        }
+        tmem_ld_wait();
+    };
+
+    auto scatter = [&](int t, const uint32_t (&dr)[MAXC][8]) {
         const int64_t jc = (int64_t)t * 128 + m;
         const bool valid = jc < Nc;
         const int64_t jcc = valid ? jc : Nc - 1;
-        const uint32_t cm = __ldg(p.cmask + jcc);
-        const uint32_t dcol = tbase + lane_base + (uint32_t)(2 * P + slot0);
 #pragma unroll
-        for (int b0 = 0; b0 < NH; b0 += SB) {
-            uint32_t tw[SB / 2];
+        for (int k = 0; k < MAXC; ++k) {
+            const int c = wq + 4 * k;
+            if (c < NCH) {
+                const uint4 w4 = __ldg(p.tslot8 + (int64_t)c * Nc + jcc);
+                const uint32_t w[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
-            for (int i = 0; i < SB; i += 2)
-                if (b0 + i < NH)
-                    tw[i / 2] = __ldg(p.tslot2 + (int64_t)((slot0 + b0 + i) >> 1) * Nc + jcc);
-#pragma unroll
-            for (int c = 0; c < SB; c += 8) {
-                if (b0 + c < NH) {
-                    uint32_t r[8];
-                    tmem_ld8(dcol + (uint32_t)(b0 + c), r);
-                    tmem_ld_wait();
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int i = c + u;
-                        const int s = slot0 + b0 + i;
-                        const uint32_t tg = (tw[i / 2] >> (16 * (i & 1))) & 0xFFFFu;
-                        if (valid && s < NS && tg != 0xFFFFu) {
-                            float g = __uint_as_float(r[u]) * unscale;
-                            if (__popc(cm & betw[s]) & 1) g = -g;
-                            atomicAdd(srow + tg, g);
-                        }
-                    }
+                for (int u = 0; u < 8; ++u) {
+                    const uint32_t e = (w[u >> 1] >> (16 * (u & 1))) & 0xFFFFu;
+                    const uint32_t tg = e & 0x7FFFu;
+                    const int q = __float2int_rn(__uint_as_float(dr[k][u]) * unscale);
+                    if (valid && tg != absent) atomicAdd(srow + tg, (e & 0x8000u) ? -q : q);
                 }
             }
         }
     };
 
-    for (int64_t ir = blockIdx.x; ir < p.Nr; ir += gridDim.x) {
-        for (int64_t j = tid; j < Nc; j += TC_THREADS) {
-            xrow[j] = p.X[ir * Nc + j];
-            srow[j] = 0.f;
+    auto wait_mma = [&]() {
+        if (tid == 0) {
+            long long t0 = clock64();
+            while (!mbar_try_wait(mbar, phase)) {
+                if (clock64() - t0 > WAIT_CYCLES) {
+                    *abort_flag = 1;
+                    atomicExch(p.err, 1);
+                    break;
+                }
+            }
         }
-        for (int s = tid; s < P; s += TC_THREADS) rowmap[s] = -1;
+        phase ^= 1u;
+    };
+
+    for (int64_t ir = blockIdx.x; ir < p.Nr; ir += gridDim.x) {
+        for (int64_t j = tid; j < Nc; j += RP_THREADS) {
+            xrow[j] = p.X[ir * Nc + j];
+            srow[j] = 0;
+        }
+        if (tid == 0) {
+            xrow[Nc] = 0.f;
+            srow[Nc] = 0;
+        }
+        for (int s = tid; s < P; s += RP_THREADS) {
+            ma[s] = (s == NS) ? sa : 0.f;   // identity column: X[R, J] itself (one-body k row)
+            rj[s] = (int32_t)ir;
+        }
         __syncthreads();
-        for (int e = tid; e < p.rnexc; e += TC_THREADS) {
+        for (int e = tid; e < p.rnexc; e += RP_THREADS) {
             const int g = p.rpq[ir * p.rnexc + e];
             int a = g / p.n, b = g % p.n;
             if (a > b) { int t = a; a = b; b = t; }
             const int s = b * (b + 1) / 2 + a;
-            rowmap[s] = (p.rtgt[ir * p.rnexc + e] << 1) | (p.rsgn[ir * p.rnexc + e] < 0 ? 1 : 0);
+            ma[s] = p.rsgn[ir * p.rnexc + e] < 0 ? -sa : sa;
+            rj[s] = p.rtgt[ir * p.rnexc + e];
         }
         __syncthreads();
 
@@ -398,23 +410,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_rowpass(const RowPass p) {
             tc_fence_after();
             issue(0);
         }
+        if (ntiles > 1) build(1, 1);
         for (int t = 0; t < ntiles; ++t) {
-            if (t + 1 < ntiles) build(t + 1, (t + 1) & 1);
-            if (tid == 0) {
-                long long t0 = clock64();
-                while (!mbar_try_wait(mbar, phase)) {
-                    if (clock64() - t0 > WAIT_CYCLES) {
-                        *abort_flag = 1;
-                        atomicExch(p.err, 1);
-                        break;
-                    }
-                }
-            }
-            phase ^= 1u;
+            wait_mma();
             __syncthreads();
             if (*abort_flag) break;
             tc_fence_after();
-            epilogue(t);
+            uint32_t dr[MAXC][8];
+            load_d(dr);
             tmem_st_wait();
             tc_fence_before();
             __syncthreads();
@@ -422,10 +425,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_rowpass(const RowPass p) {
                 tc_fence_after();
                 issue(t + 1);
             }
+            if (t + 2 < ntiles) build(t + 2, t & 1);
+            scatter(t, dr);
         }
         __syncthreads();
         if (*abort_flag) break;
-        for (int64_t j = tid; j < Nc; j += TC_THREADS) p.Y[ir * Nc + j] = srow[j];
+        for (int64_t j = tid; j < Nc; j += RP_THREADS) p.Y[ir * Nc + j] = (float)srow[j] * inv_fx;
         __syncthreads();
     }
     tc_fence_before();
@@ -492,17 +497,27 @@ __global__ void k_wimg(const double* __restrict__ h1, const double* __restrict__
     }
 }
 
-// slot table: for string j and its entry (pq -> tgt), slot s = {p,q} -> tgt, stored
-// as 16-bit pairs: word (s/2, j) holds slots 2*(s/2) (low half) and 2*(s/2)+1.
+// slot table: for string j and its entry (pq -> tgt, sgn), slot s = {p,q} holds
+// tgt | (sgn < 0) << 15; slots without an entry hold ns.  Stored per chunk of 8
+// slots: the 128-bit word (s/8, j) holds slots 8*(s/8) .. 8*(s/8)+7, slot s in
+// 16-bit half s%8.
+__global__ void k_slot_fill(uint16_t* __restrict__ tslot, int64_t count, uint16_t v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        tslot[i] = v;
+}
+
 __global__ void k_slot_table(const int32_t* __restrict__ tgt, const uint16_t* __restrict__ pq,
-                             int64_t ns, int nexc, int n, uint16_t* __restrict__ tslot) {
+                             const int8_t* __restrict__ sgn, int64_t ns, int nexc, int n,
+                             uint16_t* __restrict__ tslot) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ns * nexc) return;
     const int64_t j = i / nexc;
     int a = pq[i] / n, b = pq[i] % n;
     if (a > b) { int t = a; a = b; b = t; }
     const int s = b * (b + 1) / 2 + a;
-    tslot[((int64_t)(s >> 1) * ns + j) * 2 + (s & 1)] = (uint16_t)tgt[i];
+    tslot[((int64_t)(s >> 3) * ns + j) * 8 + (s & 7)] =
+        (uint16_t)(tgt[i] | (sgn[i] < 0 ? 0x8000 : 0));
 }
 
 // out[c][r] = in[r][c] for an R x C matrix.
@@ -544,7 +559,7 @@ uint32_t tmem_cols(int P) {
 }
 
 size_t rowpass_smem(int P, int NW, int64_t Nc) {
-    return (size_t)2 * NW * P * P + 8 * (size_t)Nc + 8 * (size_t)P + 64;
+    return (size_t)2 * NW * P * P + 8 * (size_t)(Nc + 1) + 8 * (size_t)P + 64;
 }
 
 template <int P>
@@ -570,7 +585,8 @@ void* rowpass_kernel(int P, bool fp16) {
 }  // namespace
 
 void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
-                   const double* d_eri, int norb, double wmax, bool use_fp16, cudaStream_t st) {
+                   const double* d_eri, int norb, double wmax, double wcolsum, bool use_fp16,
+                   cudaStream_t st) {
     ta = &A;
     tb = &B;
     n = norb;
@@ -582,7 +598,7 @@ void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
     fp16 = use_fp16;
     nw = fp16 ? 3 : 2;
     kernel = rowpass_kernel(P, fp16);
-    if (!kernel || tmem_cols(P) > 512)
+    if (!kernel || tmem_cols(P) > 512 || A.ns > 32766 || B.ns > 32766)
         KPM_THROW(KPM_EUNSUPPORTED, "tensor-core sigma supports up to 16 orbitals");
     int dev = 0;
     KPM_CUDA(cudaGetDevice(&dev));
@@ -591,6 +607,7 @@ void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
     if (prop.major != 10)
         KPM_THROW(KPM_EUNSUPPORTED, "tensor-core sigma needs a Blackwell (sm_10x) GPU");
     nsm = prop.multiProcessorCount;
+    gbound = (float)(wcolsum * (1.0 + 1e-6));
     int64_t ncmax = nsa > nsb ? nsa : nsb;
     smem_bytes = rowpass_smem(P, nw, ncmax);
     // at least ~116 KB so that exactly one CTA (and one TMEM allocation) fits per SM
@@ -620,13 +637,15 @@ void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
     KPM_LAUNCHED();
 
     auto build_slots = [&](const SpinTables& T, DevBuf& out) {
-        size_t bytes = (size_t)P * T.ns * sizeof(uint16_t);
-        out.alloc(bytes);
-        KPM_CUDA(cudaMemsetAsync(out.p, 0xFF, bytes, st));
+        size_t count = (size_t)P * T.ns;
+        out.alloc(count * sizeof(uint16_t));
+        k_slot_fill<<<1024, 256, 0, st>>>(out.as<uint16_t>(), (int64_t)count, (uint16_t)T.ns);
+        KPM_LAUNCHED();
         int64_t ne = T.ns * T.nexc;
         if (ne > 0) {
             k_slot_table<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
-                T.tgt.as<int32_t>(), T.pq.as<uint16_t>(), T.ns, T.nexc, n, out.as<uint16_t>());
+                T.tgt.as<int32_t>(), T.pq.as<uint16_t>(), T.sgn.as<int8_t>(), T.ns, T.nexc, n,
+                out.as<uint16_t>());
             KPM_LAUNCHED();
         }
     };
@@ -644,33 +663,31 @@ void TcSigma::apply(const float* x, float* y, int ncol, cudaStream_t st) {
     for (int c = 0; c < ncol; ++c) {
         const float* X = x + (size_t)c * dim;
         float* Y = y + (size_t)c * dim;
-        const float* am = nullptr;
-        if (fp16) {
-            // both passes read the same numbers (x and its transpose)
-            KPM_CUDA(cudaMemsetAsync(amax.p, 0, sizeof(unsigned), st));
-            k_absmax<<<1024, 256, 0, st>>>(X, dim, amax.as<unsigned>());
-            KPM_LAUNCHED();
-            am = reinterpret_cast<const float*>(amax.p);
-        }
+        // max|x|: FP16 operand scale and fixed-point range; both passes read the
+        // same numbers (x and its transpose)
+        KPM_CUDA(cudaMemsetAsync(amax.p, 0, sizeof(unsigned), st));
+        k_absmax<<<1024, 256, 0, st>>>(X, dim, amax.as<unsigned>());
+        KPM_LAUNCHED();
+        const float* am = reinterpret_cast<const float*>(amax.p);
         // pass 1: rows alpha, columns beta, opposite-spin part on
-        RowPass p1{X, Y, nsa, nsb, slot_b.as<uint32_t>(), tb->masks.as<uint32_t>(),
+        RowPass p1{X, Y, nsa, nsb, slot_b.as<uint4>(),
                    ta->tgt.as<int32_t>(), ta->pq.as<uint16_t>(), ta->sgn.as<int8_t>(), ta->nexc,
-                   wimg.as<uint4>(), NS, n, nc, am, wscale, err.as<int>()};
+                   wimg.as<uint4>(), NS, n, nc, am, wscale, gbound, tb->nexc, err.as<int>()};
         int g1 = (int)(nsa < nsm ? nsa : nsm);
         void* args1[] = {&p1};
-        KPM_CUDA(cudaLaunchKernel(kernel, dim3(g1), dim3(TC_THREADS), args1, smem_bytes, st));
+        KPM_CUDA(cudaLaunchKernel(kernel, dim3(g1), dim3(RP_THREADS), args1, smem_bytes, st));
         KPM_LAUNCHED();
         // pass 2 on x^T: rows beta, columns alpha, same-spin alpha part only
         dim3 tb2(32, 8);
         dim3 gt((unsigned)((nsb + 31) / 32), (unsigned)((nsa + 31) / 32));
         k_transpose<<<gt, tb2, 0, st>>>(X, xt.as<float>(), nsa, nsb);
         KPM_LAUNCHED();
-        RowPass p2{xt.as<float>(), sp.as<float>(), nsb, nsa, slot_a.as<uint32_t>(),
-                   ta->masks.as<uint32_t>(), nullptr, nullptr, nullptr, 0, wimg.as<uint4>(),
-                   NS, n, nc, am, wscale, err.as<int>()};
+        RowPass p2{xt.as<float>(), sp.as<float>(), nsb, nsa, slot_a.as<uint4>(),
+                   nullptr, nullptr, nullptr, 0, wimg.as<uint4>(),
+                   NS, n, nc, am, wscale, gbound, ta->nexc, err.as<int>()};
         int g2 = (int)(nsb < nsm ? nsb : nsm);
         void* args2[] = {&p2};
-        KPM_CUDA(cudaLaunchKernel(kernel, dim3(g2), dim3(TC_THREADS), args2, smem_bytes, st));
+        KPM_CUDA(cudaLaunchKernel(kernel, dim3(g2), dim3(RP_THREADS), args2, smem_bytes, st));
         KPM_LAUNCHED();
         k_add_transposed<<<gt, tb2, 0, st>>>(Y, sp.as<float>(), nsa, nsb);
         KPM_LAUNCHED();

@@ -13,19 +13,22 @@ struct TcSigma {
     bool fp16 = false;            // operand format: split FP16 (scaled) or split BF16
     int nw = 2;                   // 16-bit pieces of W (3 for FP16, 2 for BF16)
     float wscale = 1.0f;          // power-of-two scale of W in the image
+    float gbound = 0.0f;          // max over output slots of sum over input slots of |W|
     void* kernel = nullptr;       // k_rowpass instantiation for P
     const SpinTables* ta = nullptr;
     const SpinTables* tb = nullptr;
     DevBuf wimg;                  // W = [(pq|rs) ; k] as split 16-bit operand image (hi | lo)
-    DevBuf slot_a, slot_b;        // uint16 [P][N_s] pair-slot -> target string (0xFFFF: none)
+    DevBuf slot_a, slot_b;        // uint16 [P/8][N_s][8] pair-slot -> target | sign << 15 (N_s: none)
     DevBuf xt, sp;                // workspaces: x transposed, transposed-pass output
     DevBuf err;                   // int error flag (1: a bounded wait ran out)
-    DevBuf amax;                  // max |x| (float bits) for FP16 operand scaling
+    DevBuf amax;                  // max |x| (float bits): operand scale, fixed-point range
     size_t smem_bytes = 0;
 
-    // wmax: max |W| over (pq|rs) and k_pq (host-computed), for the FP16 scale.
+    // wmax: max |W| over (pq|rs) and k_pq (host-computed), for the FP16 scale;
+    // wcolsum: max over output slots s of sum over input slots k of |W[k][s]|.
     void init(const SpinTables& ta, const SpinTables& tb, const double* d_h1,
-              const double* d_eri, int n, double wmax, bool use_fp16, cudaStream_t st);
+              const double* d_eri, int n, double wmax, double wcolsum, bool use_fp16,
+              cudaStream_t st);
     void apply(const float* x, float* y, int ncol, cudaStream_t st);
     // Reads and clears the device error flag (synchronises the stream).
     int check(cudaStream_t st);

@@ -332,3 +332,40 @@ def test_moments_mixed_8o(torch, sys8, prec):
     print(prec, "8o moment error / Omega_0:", errs)
     assert max(errs) < {"mixed": 2e-5, "mixed_bf16": 1e-2}[prec], errs
     k.close()
+
+
+def _hash_vector_dev(torch, dim):
+    """The oracle's hash test vector built on the device in chunks (exact in FP32)."""
+    x = torch.empty(dim, dtype=torch.float32, device="cuda")
+    C = 0x9E3779B97F4A7C15 - (1 << 64)          # same bits as a signed int64
+    step = 1 << 27
+    for s0 in range(0, dim, step):
+        i = torch.arange(s0, min(dim, s0 + step), device="cuda", dtype=torch.int64)
+        h = ((i * C) >> 48) & 0xFFFF            # wrap-around multiply, low 16 bits of the shift
+        x[s0:s0 + len(i)] = ((h - 32768).to(torch.float64) / 16777216.0).to(torch.float32)
+    return x
+
+
+def test_sigma_18_orbitals_sampled_rows(torch):
+    """18 orbitals, 9+9 electrons (FCI dim 2,363,904,400, int64 indexing): FP32 sigma
+    on sampled rows vs the oracle's Slater-Condon row-pull."""
+    from oracle.hamiltonian import hash_vector
+    n, m = 18, 9
+    I = synthetic.integrals(n, m, m, seed=2506075)
+    k = _kpm(I, n, m, m, "fp32")
+    dim = k.dim
+    assert dim == math.comb(18, 9) ** 2 and dim > 2**31
+    x = _hash_vector_dev(torch, dim)
+    probe = np.array([0, 1, 2**31 + 5, dim - 1])
+    assert np.array_equal(x[torch.tensor(probe, device="cuda")].cpu().numpy().astype(np.float64),
+                          hash_vector(probe))
+    y = k.sigma(x)
+    k.synchronize()
+    del x
+    sc = oracle.SlaterCondon(I.h1, I.eri, n, m, m)
+    rng = np.random.default_rng(18)
+    rows = np.concatenate([rng.choice(dim, 3000, replace=False), [0, dim - 1, 2**31 + 5]])
+    ref = sc.sigma_rows_hash(rows)
+    got = y[torch.tensor(rows, device="cuda")].cpu().numpy().astype(np.float64)
+    assert np.abs(got - ref).max() / np.abs(ref).max() < 2e-6
+    k.close()

@@ -232,6 +232,19 @@ def test_operator_form_equals_slater_condon_8o():
     assert np.abs(sc.sigma_rows(rows, x) - sc.csr()[rows] @ x).max() < 1e-12
 
 
+def test_hash_vector_row_pull_equals_dense_row_pull():
+    from oracle.hamiltonian import _lib, hash_vector
+    I = synthetic.integrals(8, 4, 4, seed=3)
+    sc = oracle.SlaterCondon(I.h1, I.eri, 8, 4, 4)
+    x = hash_vector(np.arange(sc.dim))
+    assert np.all(np.abs(x) <= 2.0 ** -9) and len(np.unique(x)) > 1000
+    assert np.array_equal(x.astype(np.float32).astype(np.float64), x)
+    for i in (0, 1, 12345, 2**31 + 7, 2**40 + 3):
+        assert _lib().sc_hashvec(i) == hash_vector([i])[0]
+    rows = np.arange(0, sc.dim, 13)
+    assert np.abs(sc.sigma_rows_hash(rows) - sc.sigma_rows(rows, x)).max() < 1e-15
+
+
 # ---------------------------------------------------------------- KPM
 
 @pytest.mark.parametrize("N", [2, 16, 256, 2048])

@@ -1,0 +1,99 @@
+"""Continuous-batching server: results alone == results in the mix, admission
+by device memory, cancellation, and parity of a served request with the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+from oracle import kpm as okpm
+
+pytestmark = pytest.mark.gpu
+
+# (norb, electrons per spin, seed, moments)
+REQS = [(8, 4, 2506101, 128), (6, 3, 2506102, 64), (10, 5, 2506103, 96), (8, 3, 2506104, 160),
+        (7, 3, 2506105, 64), (10, 5, 2506106, 128)]
+
+
+def _inputs(n, m, seed):
+    I = synthetic.integrals(n, m, m, seed)
+    sc = oracle.SlaterCondon(I.h1, I.eri, n, m, m)
+    psi = synthetic.random_state(sc.dim, seed + 7)
+    emin, emax = (None, None)
+    if sc.dim <= 5000:
+        w = np.linalg.eigvalsh(sc.dense())
+        emin, emax = w[0], w[-1]
+    else:
+        sc.csr()
+        emin, emax = oracle.spectral_bounds(sc.sigma, sc.dim)
+    a, b = okpm.scale_from_bounds(emin, emax)
+    return I, sc, psi, a, b
+
+
+@pytest.fixture(scope="module")
+def cases():
+    return [(n, m, nm) + _inputs(n, m, seed) for n, m, seed, nm in REQS]
+
+
+def _submit(srv, case, mask=0b111):
+    n, m, nm, I, sc, psi, a, b = case
+    return srv.submit(I.h1, I.eri, I.dipole, n, m, m, psi, mask, a, b, nm, npoints=256)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_same_alone_and_in_mix(cases, prec):
+    from paper_2506_07430_gb300 import Server
+    srv = Server(mem_budget_bytes=4 << 30, max_slots=4, steps_per_round=8, precision=prec)
+    alone = []
+    for c in cases:
+        alone.append(srv.wait(_submit(srv, c)))
+    ids = [_submit(srv, c) for c in cases]
+    mix = [srv.wait(i) for i in ids]
+    srv.close()
+    for r0, r1 in zip(alone, mix):
+        # fixed launch shapes, fixed-order reductions and (tensor-core path) integer
+        # accumulation of the scattered sums: bitwise identical alone and in the mix
+        assert np.array_equal(r0["omega"], r1["omega"])
+        assert np.array_equal(r0["moments"], r1["moments"])
+        assert np.array_equal(r0["intensity"], r1["intensity"])
+
+
+def test_served_request_matches_oracle(cases):
+    from paper_2506_07430_gb300 import Server
+    n, m, nm, I, sc, psi, a, b = cases[0]
+    srv = Server(mem_budget_bytes=1 << 30, max_slots=2, steps_per_round=16, precision="fp64")
+    r = srv.wait(_submit(srv, cases[0], mask=0b011))
+    srv.close()
+    for c in range(2):
+        ref = okpm.moments_recursion(sc.sigma, sc.dipole(I.dipole[c], psi), a, b, nm)
+        assert np.abs(r["moments"][c] - ref).max() < 1e-10 * ref[0]
+    om_r, it_r = okpm.spectrum(r["moments"].sum(axis=0), a, b, 256)
+    assert np.linalg.norm(r["intensity"] - it_r) < 1e-10 * np.linalg.norm(it_r)
+    assert r["t_total_s"] >= r["t_run_s"] >= 0.0
+
+
+def test_admission_respects_memory_budget(cases):
+    from paper_2506_07430_gb300 import Server
+    big = [c for c in cases if c[0] == 10]
+    # one 10o request is estimated at ~70 MB (fp64, 3 columns): a 100 MB budget holds
+    # one at a time, so the requests must run one after the other
+    srv = Server(mem_budget_bytes=100 << 20, max_slots=4, steps_per_round=8,
+                 precision="fp64")
+    ids = [_submit(srv, c) for c in big]
+    res = [srv.wait(i) for i in ids]
+    srv.close()
+    iv = sorted((r["t_queue_s"], r["t_queue_s"] + r["t_run_s"]) for r in res)
+    for (s0, e0), (s1, e1) in zip(iv, iv[1:]):
+        assert s1 >= e0 - 1e-3, iv
+
+
+def test_cancel_and_timeout(cases):
+    from paper_2506_07430_gb300 import KPMError, Server
+    srv = Server(mem_budget_bytes=4 << 30, max_slots=1, steps_per_round=4, precision="fp64")
+    i0 = _submit(srv, cases[2])
+    i1 = _submit(srv, cases[5])
+    srv.cancel(i1)
+    with pytest.raises(KPMError, match="KPM_ECANCELLED"):
+        srv.wait(i1)
+    r0 = srv.wait(i0)
+    assert r0["status"] == 0
+    srv.close()
