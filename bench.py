@@ -49,7 +49,7 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="fci16o16e")
-    p.add_argument("--precision", choices=["fp64", "fp32", "mixed", "mixed_bf16"], default="fp32")
+    p.add_argument("--precision", choices=["fp64", "fp32", "mixed", "mixed_bf16"], default="mixed")
     p.add_argument("--chunk", type=int, default=None, help="Chebyshev steps per bench step")
     p.add_argument("--lanczos", type=int, default=24, help="Lanczos steps for a, b (untimed)")
     p.add_argument("--e2e-requests", type=int, default=2)
