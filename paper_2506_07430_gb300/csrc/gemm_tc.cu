@@ -1,0 +1,527 @@
+// Dense same-spin products on tcgen05 tensor cores.
+//
+// The same-spin part of H acts on the vector C[I_a][I_b] as
+//   sigma_bb[I_a][I_b] = sum_J F_b[I_b][J] C[I_a][J]      (beta string Hamiltonian)
+//   sigma_aa[I_a][I_b] = sum_J F_a[I_a][J] C[J][I_b]      (alpha string Hamiltonian)
+// F_s is the Slater-Condon matrix of one spin's strings (tables.cu), symmetric,
+// with about 6.6 % nonzeros at 16 orbitals and no useful block sparsity at
+// 128 x 128 tiles (83 % of the tiles hold a nonzero), so both products run as
+// dense GEMMs: out[m][n] = sum_k A[m][k] B[n][k] with both operands K-major,
+//   beta:  A = F_b (m = I_b, k = J),      B = C (n = I_a, k = J)
+//   alpha: A = C^T (m = I_b, k = J),      B = F_a (n = I_a, k = J)
+// and in both cases the epilogue adds out[m][n] into y[n * ldy + m], so the 32
+// lanes of a warp (consecutive m) write consecutive addresses.
+//
+// Operands are split into two FP16 pieces with power-of-two scales (x = hi + lo);
+// three MMAs per k-step (A_hi B_hi + A_lo B_hi + A_hi B_lo) accumulate in FP32
+// in tensor memory.  The diagonals of F_a, F_b are kept out of the split matrices
+// and added exactly in the epilogue of the alpha product (FP64 values stored as
+// float hi + lo), together with nothing else.
+//
+// Kernel: CTA tile 128 x 256, k-block 64 (128 bytes per row: one SWIZZLE_128B
+// atom row), two-stage TMA pipeline (full/empty mbarriers), one thread issues
+// TMA, one issues MMAs, four warps run the epilogue.  All waits are bounded.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_fp16.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "gemm_tc.cuh"
+
+namespace kpm {
+namespace {
+
+constexpr int GM_BM = 128, GM_BN = 256, GM_BK = 64, GM_STAGES = 2;
+constexpr int GM_THREADS = 128;
+constexpr uint32_t A_BYTES = GM_BM * GM_BK * 2;  // 16 KB per piece
+constexpr uint32_t B_BYTES = GM_BN * GM_BK * 2;  // 32 KB per piece
+constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+constexpr long long GM_WAIT = 4000000000LL;
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init_(uint64_t* b, uint32_t c) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(c) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok) : "r"(su32(b)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// bounded wait; returns false (and flags the error) if it ran out
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* b, uint32_t parity, int* err) {
+    long long t0 = clock64();
+    while (!mbar_test(b, parity)) {
+        if (clock64() - t0 > GM_WAIT) {
+            atomicExch(err, 1);
+            return false;
+        }
+    }
+    return true;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(su32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+__device__ __forceinline__ void tc_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void mma_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                       uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
+__device__ __forceinline__ void mma_commit_(uint64_t* b) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// K-major SWIZZLE_128B descriptor: 8-row x 128-byte atoms, SBO = 1024 bytes
+// between atoms along M/N; the leading offset is unused for this layout.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;                 // LBO (ignored)
+    d |= (uint64_t)(1024 >> 4) << 32;       // SBO
+    d |= (uint64_t)1 << 46;                 // version
+    d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
+    return d;
+}
+
+__host__ __device__ constexpr uint32_t gemm_idesc() {
+    // D F32, A/B F16, K-major, N = 256, M = 128
+    return (1u << 4) | ((uint32_t)(GM_BN >> 3) << 17) | ((uint32_t)(GM_BM >> 4) << 24);
+}
+
+struct GemmArgs {
+    int M, N, K;               // out is M x N; operands have K columns
+    float* y;                  // y[n * ldy + m] += scale * out[m][n]
+    int64_t ldy;
+    float scale;               // or, if amax != nullptr, scale / (sa(amax)) with the operand scale
+    const float* amax;         // max |x| of the split vector operand (operand scale), or null
+    float wscale;              // scale of the matrix operand
+    // exact diagonal term: y[n*ldy+m] += (dn[n] + dm[m]) * x[n*ldy+m]  (if x != nullptr)
+    const float* x;
+    const float2* dm;
+    const float2* dn;
+    int* err;
+};
+
+__global__ void __launch_bounds__(GM_THREADS, 1)
+k_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+       const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
+       const GemmArgs g) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + GM_STAGES * STAGE_BYTES);
+    uint64_t* empty = full + GM_STAGES;
+    uint64_t* done = empty + GM_STAGES;
+    uint32_t* holder = reinterpret_cast<uint32_t*>(done + 1);
+    int* abort_flag = reinterpret_cast<int*>(holder + 1);
+    int* issued = abort_flag + 1;     // stages whose TMA loads were issued
+    int* consumed = issued + 1;       // stages whose full barrier the MMA thread passed
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * GM_BM, n0 = blockIdx.y * GM_BN;
+    const int nk = (g.K + GM_BK - 1) / GM_BK;
+
+    if (tid == 0) {
+        for (int s = 0; s < GM_STAGES; ++s) {
+            mbar_init_(&full[s], 1);
+            mbar_init_(&empty[s], 1);
+        }
+        mbar_init_(done, 1);
+        *abort_flag = 0;
+        *issued = 0;
+        *consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        prefetch_map(&mA0);
+        prefetch_map(&mA1);
+        prefetch_map(&mB0);
+        prefetch_map(&mB1);
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;"
+                     ::"r"(su32(holder)) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_before();
+    __syncthreads();
+    tc_after();
+    const uint32_t tmem = *holder;
+
+    if (tid == 0) {
+        // TMA producer
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % GM_STAGES;
+            if (kb >= GM_STAGES) {
+                if (!mbar_wait_bounded(&empty[s], ((kb / GM_STAGES) - 1) & 1, g.err)) {
+                    *abort_flag = 1;
+                    break;
+                }
+            }
+            unsigned char* st = smem + s * STAGE_BYTES;
+            mbar_expect_tx(&full[s], STAGE_BYTES);
+            const int kx = kb * GM_BK;
+            tma_load_2d(su32(st), &mA0, kx, m0, &full[s]);
+            tma_load_2d(su32(st + A_BYTES), &mA1, kx, m0, &full[s]);
+            tma_load_2d(su32(st + 2 * A_BYTES), &mB0, kx, n0, &full[s]);
+            tma_load_2d(su32(st + 2 * A_BYTES + B_BYTES), &mB1, kx, n0, &full[s]);
+            *(volatile int*)issued = kb + 1;
+        }
+    } else if (tid == 32) {
+        // MMA issuer
+        constexpr uint32_t idesc = gemm_idesc();
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % GM_STAGES;
+            if (!mbar_wait_bounded(&full[s], (kb / GM_STAGES) & 1, g.err)) {
+                *abort_flag = 1;
+                break;
+            }
+            *(volatile int*)consumed = kb + 1;
+            tc_after();
+            const uint32_t st = su32(smem + s * STAGE_BYTES);
+            const uint32_t a0 = st, a1 = st + A_BYTES, b0 = st + 2 * A_BYTES,
+                           b1 = st + 2 * A_BYTES + B_BYTES;
+#pragma unroll
+            for (int j = 0; j < GM_BK / 16; ++j) {
+                const uint32_t off = j * 32;  // 16 FP16 = 32 bytes along K in the atom row
+                const uint32_t acc0 = (kb | j) != 0;
+                mma_ss(tmem, sw128_desc(a0 + off), sw128_desc(b0 + off), idesc, acc0);
+                mma_ss(tmem, sw128_desc(a1 + off), sw128_desc(b0 + off), idesc, 1);
+                mma_ss(tmem, sw128_desc(a0 + off), sw128_desc(b1 + off), idesc, 1);
+            }
+            mma_commit_(&empty[s]);
+        }
+        mma_commit_(done);
+    }
+    __syncwarp();
+    // epilogue: every thread waits for the last MMAs
+    bool ok = mbar_wait_bounded(done, 0, g.err);
+    __syncthreads();
+    if (*abort_flag) ok = false;
+    tc_after();
+    float scale = g.scale / g.wscale;
+    if (g.amax) {
+        const float mx = *g.amax;
+        if (mx > 0.f && isfinite(mx)) {
+            int e;
+            frexpf(mx, &e);
+            scale = scale / ldexpf(1.f, 14 - max(e, -90));
+        }
+    }
+    const int m = m0 + warp * 32 + lane;
+    const bool mval = m < g.M;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    float2 dmv = make_float2(0.f, 0.f);
+    if (g.x && mval) dmv = g.dm[m];
+#pragma unroll 1
+    for (int c = 0; c < GM_BN; c += 32) {
+        uint32_t r[32];
+        ld32(trow + (uint32_t)c, r);
+        if (!ok || !mval) continue;
+#pragma unroll 8
+        for (int u = 0; u < 32; ++u) {
+            const int n = n0 + c + u;
+            if (n < g.N) {
+                const int64_t o = (int64_t)n * g.ldy + m;
+                float v = g.y[o] + __uint_as_float(r[u]) * scale;
+                if (g.x) {
+                    const float2 dn = g.dn[n];
+                    const float xv = g.x[o];
+                    v = fmaf(dmv.x + dn.x, xv, fmaf(dmv.y + dn.y, xv, v));
+                }
+                g.y[o] = v;
+            }
+        }
+    }
+    tc_before();
+    __syncthreads();
+    if (tid == 0 && *abort_flag) {
+        // after an abort, wait (bounded) for TMA copies that were issued but not consumed
+        for (int kb = *consumed; kb < *issued; ++kb)
+            mbar_wait_bounded(&full[kb % GM_STAGES], (kb / GM_STAGES) & 1, g.err);
+    }
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem)
+                     : "memory");
+}
+
+// max |F[t][r]| over off-diagonal entries t >= 1 (bits of a non-negative double)
+__global__ void k_absmax_offdiag(const double* __restrict__ fval, int64_t ns, int nnbr,
+                                 unsigned long long* out) {
+    double mx = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ns * (nnbr - 1);
+         i += (int64_t)gridDim.x * blockDim.x)
+        mx = fmax(mx, fabs(fval[ns + i]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(mx));
+}
+
+// Split rows: src[r][c] (float, r < R, c < Cn, row pitch ld) -> hi/lo FP16 [r][pitch],
+// scaled by 2^(14 - e(amax)); pad columns [Cn, pitch) with zeros.
+__global__ void k_split_rows(const float* __restrict__ src, int64_t R, int64_t Cn, int64_t ld,
+                             __half* __restrict__ hi, __half* __restrict__ lo, int64_t pitch,
+                             const float* amax) {
+    float sa = 1.f;
+    {
+        const float mx = *amax;
+        if (mx > 0.f && isfinite(mx)) {
+            int e;
+            frexpf(mx, &e);
+            sa = ldexpf(1.f, 14 - max(e, -90));
+        }
+    }
+    const int64_t total = R * pitch;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / pitch, c = i % pitch;
+        const float v = c < Cn ? src[r * ld + c] * sa : 0.f;
+        const __half h = __float2half_rn(v);
+        hi[i] = h;
+        lo[i] = __float2half_rn(v - __half2float(h));
+    }
+}
+
+// Transposed split: dst[c][r] = src[r][c] for src R x Cn, dst rows Cn of pitch >= R.
+__global__ void k_split_transpose(const float* __restrict__ src, int64_t R, int64_t Cn,
+                                  __half* __restrict__ hi, __half* __restrict__ lo,
+                                  int64_t pitch, const float* amax) {
+    __shared__ float t[32][33];
+    float sa = 1.f;
+    {
+        const float mx = *amax;
+        if (mx > 0.f && isfinite(mx)) {
+            int e;
+            frexpf(mx, &e);
+            sa = ldexpf(1.f, 14 - max(e, -90));
+        }
+    }
+    const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int64_t r = r0 + k, c = c0 + threadIdx.x;
+        t[k][threadIdx.x] = (r < R && c < Cn) ? src[r * Cn + c] * sa : 0.f;
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int64_t c = c0 + k, r = r0 + threadIdx.x;
+        if (c < Cn && r < pitch) {
+            const float v = t[threadIdx.x][k];
+            const __half h = __float2half_rn(v);
+            hi[c * pitch + r] = h;
+            lo[c * pitch + r] = __float2half_rn(v - __half2float(h));
+        }
+    }
+}
+
+// Dense off-diagonal string Hamiltonian, split into two scaled FP16 pieces.
+// The matrix is first zeroed (k_zero_half), then every off-diagonal neighbour
+// entry (t >= 1 of the [nnbr][ns] lists) is written.
+__global__ void k_dense_offdiag(const int32_t* __restrict__ fcol, const double* __restrict__ fval,
+                                int64_t ns, int nnbr, double wscale, __half* __restrict__ hi,
+                                __half* __restrict__ lo, int64_t pitch) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ns * (nnbr - 1)) return;
+    const int64_t t = 1 + i / ns, r = i % ns;
+    const int64_t c = fcol[t * ns + r];
+    const double v = fval[t * ns + r] * wscale;
+    const __half h = __double2half(v);
+    hi[r * pitch + c] = h;
+    lo[r * pitch + c] = __double2half(v - (double)__half2float(h));
+}
+
+__global__ void k_zero_half(__half* p, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = __float2half(0.f);
+}
+
+// diag[r] = F[r][r] (entry t = 0), as float hi + lo.
+__global__ void k_diag_pair(const double* __restrict__ fval, int64_t ns, float2* __restrict__ d) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= ns) return;
+    const double v = fval[r];
+    const float h = (float)v;
+    d[r] = make_float2(h, (float)(v - (double)h));
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// 2-D FP16 tensor map: rows x cols (cols innermost, row pitch in elements),
+// box = 64 columns x box_rows rows, 128-byte swizzle, zero fill out of bounds.
+CUtensorMap make_map(const __half* base, int64_t rows, int64_t cols, int64_t pitch, int box_rows) {
+    auto fn = encode_fn();
+    if (!fn) KPM_THROW(KPM_ECUDA, "cuTensorMapEncodeTiled is not available");
+    if (((uintptr_t)base & 15) || ((pitch * 2) & 15))
+        KPM_THROW(KPM_EINVAL, "tensor map base/pitch not 16-byte aligned");
+    CUtensorMap m;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(pitch * 2)};
+    cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (void*)base, dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) KPM_THROW(KPM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return m;
+}
+
+}  // namespace
+
+int64_t half_pitch(int64_t cols) { return (cols + 7) / 8 * 8; }
+
+static double offdiag_scale(const SpinTables& T, DevBuf& scratch, cudaStream_t st) {
+    scratch.ensure(sizeof(unsigned long long));
+    KPM_CUDA(cudaMemsetAsync(scratch.p, 0, sizeof(unsigned long long), st));
+    if (T.nnbr > 1) {
+        k_absmax_offdiag<<<1024, 256, 0, st>>>(T.fval64.as<double>(), T.ns, T.nnbr,
+                                               scratch.as<unsigned long long>());
+        KPM_LAUNCHED();
+    }
+    unsigned long long bits = 0;
+    KPM_CUDA(cudaMemcpyAsync(&bits, scratch.p, sizeof(bits), cudaMemcpyDeviceToHost, st));
+    KPM_CUDA(cudaStreamSynchronize(st));
+    double mx;
+    std::memcpy(&mx, &bits, sizeof(mx));
+    if (!(mx > 0.0)) return 1.0;
+    int e;
+    std::frexp(mx, &e);  // mx < 2^e
+    return std::ldexp(1.0, 14 - e);
+}
+
+static void build_f(const SpinTables& T, double ws, DevBuf& hi, DevBuf& lo, DevBuf& dg,
+                    int64_t pitch, cudaStream_t st) {
+    const int64_t n = T.ns * pitch;
+    hi.alloc(n * 2);
+    lo.alloc(n * 2);
+    k_zero_half<<<1024, 256, 0, st>>>(hi.as<__half>(), n);
+    KPM_LAUNCHED();
+    k_zero_half<<<1024, 256, 0, st>>>(lo.as<__half>(), n);
+    KPM_LAUNCHED();
+    const int64_t ne = T.ns * (int64_t)(T.nnbr - 1);
+    if (ne > 0) {
+        k_dense_offdiag<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
+            T.fcol.as<int32_t>(), T.fval64.as<double>(), T.ns, T.nnbr, ws, hi.as<__half>(),
+            lo.as<__half>(), pitch);
+        KPM_LAUNCHED();
+    }
+    dg.alloc(T.ns * sizeof(float2));
+    k_diag_pair<<<(unsigned)((T.ns + 255) / 256), 256, 0, st>>>(T.fval64.as<double>(), T.ns,
+                                                                 dg.as<float2>());
+    KPM_LAUNCHED();
+}
+
+void DenseSS::init(const SpinTables& A, const SpinTables& B, bool same, int* err_flag,
+                   cudaStream_t st) {
+    na = A.ns;
+    nb = B.ns;
+    pa = half_pitch(na);
+    pb = half_pitch(nb);
+    err = err_flag;
+    smem = GM_STAGES * STAGE_BYTES + 1024 + 256;
+    KPM_CUDA(cudaFuncSetAttribute(k_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    wscale_b = offdiag_scale(B, fmax, st);
+    build_f(B, wscale_b, fb_hi, fb_lo, db, pb, st);
+    if (same) {
+        wscale_a = wscale_b;
+        fa_hi = &fb_hi;
+        fa_lo = &fb_lo;
+        da = &db;
+    } else {
+        wscale_a = offdiag_scale(A, fmax, st);
+        build_f(A, wscale_a, fa_hi_own, fa_lo_own, da_own, pa, st);
+        fa_hi = &fa_hi_own;
+        fa_lo = &fa_lo_own;
+        da = &da_own;
+    }
+}
+
+void DenseSS::apply(const float* x, float* y, const float* amax, cudaStream_t st) {
+    // split copies of x: rows (alpha) x cols (beta), and transposed
+    xh.ensure((size_t)na * pb * 2);
+    xl.ensure((size_t)na * pb * 2);
+    th.ensure((size_t)nb * pa * 2);
+    tl.ensure((size_t)nb * pa * 2);
+    k_split_rows<<<2048, 256, 0, st>>>(x, na, nb, nb, xh.as<__half>(), xl.as<__half>(), pb, amax);
+    KPM_LAUNCHED();
+    dim3 tb(32, 8), gt((unsigned)((nb + 31) / 32), (unsigned)((na + 31) / 32));
+    k_split_transpose<<<gt, tb, 0, st>>>(x, na, nb, th.as<__half>(), tl.as<__half>(), pa, amax);
+    KPM_LAUNCHED();
+    // beta: out[m = I_b][n = I_a] = sum_J Fb[I_b][J] x[I_a][J]
+    {
+        CUtensorMap a0 = make_map(fb_hi.as<__half>(), nb, nb, pb, GM_BM);
+        CUtensorMap a1 = make_map(fb_lo.as<__half>(), nb, nb, pb, GM_BM);
+        CUtensorMap b0 = make_map(xh.as<__half>(), na, nb, pb, GM_BN);
+        CUtensorMap b1 = make_map(xl.as<__half>(), na, nb, pb, GM_BN);
+        GemmArgs g{(int)nb, (int)na, (int)nb, y, nb, 1.0f, amax, (float)wscale_b,
+                   nullptr, nullptr, nullptr, err};
+        dim3 grid((unsigned)((nb + GM_BM - 1) / GM_BM), (unsigned)((na + GM_BN - 1) / GM_BN));
+        k_gemm<<<grid, GM_THREADS, smem, st>>>(a0, a1, b0, b1, g);
+        KPM_LAUNCHED();
+    }
+    // alpha: out[m = I_b][n = I_a] = sum_J x^T[I_b][J] Fa[I_a][J], plus the exact diagonals
+    {
+        CUtensorMap a0 = make_map(th.as<__half>(), nb, na, pa, GM_BM);
+        CUtensorMap a1 = make_map(tl.as<__half>(), nb, na, pa, GM_BM);
+        CUtensorMap b0 = make_map(fa_hi->as<__half>(), na, na, pa, GM_BN);
+        CUtensorMap b1 = make_map(fa_lo->as<__half>(), na, na, pa, GM_BN);
+        GemmArgs g{(int)nb, (int)na, (int)na, y, nb, 1.0f, amax, (float)wscale_a,
+                   x, db.as<float2>(), da->as<float2>(), err};
+        dim3 grid((unsigned)((nb + GM_BM - 1) / GM_BM), (unsigned)((na + GM_BN - 1) / GM_BN));
+        k_gemm<<<grid, GM_THREADS, smem, st>>>(a0, a1, b0, b1, g);
+        KPM_LAUNCHED();
+    }
+}
+
+}  // namespace kpm

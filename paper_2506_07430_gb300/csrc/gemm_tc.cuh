@@ -1,0 +1,31 @@
+// Dense same-spin products on tcgen05 tensor cores (see gemm_tc.cu).
+#pragma once
+#include "common.cuh"
+
+namespace kpm {
+
+// Row pitch (elements) of an FP16 matrix with `cols` columns: 16-byte rows.
+int64_t half_pitch(int64_t cols);
+
+// sigma += F_b-part + F_a-part of H applied to x (FP32 [N_a][N_b]); see gemm_tc.cu.
+struct DenseSS {
+    int64_t na = 0, nb = 0, pa = 0, pb = 0;   // strings and FP16 row pitches per spin
+    double wscale_a = 1.0, wscale_b = 1.0;    // power-of-two scales of the split matrices
+    DevBuf fa_hi_own, fa_lo_own, da_own;      // alpha matrices (own copy if N_a != N_b)
+    DevBuf fb_hi, fb_lo, db;                  // beta matrices, diagonal of F_b (float hi/lo)
+    DevBuf* fa_hi = nullptr;
+    DevBuf* fa_lo = nullptr;
+    DevBuf* da = nullptr;
+    DevBuf xh, xl, th, tl;                    // split copies of x and x^T
+    DevBuf fmax;                              // scratch for max |F_off|
+    size_t smem = 0;
+    int* err = nullptr;
+
+    // Builds the split matrices; `same`: alpha and beta strings are identical.
+    void init(const SpinTables& A, const SpinTables& B, bool same, int* err_flag,
+              cudaStream_t st);
+    // y += (F_a (x) 1 + 1 (x) F_b) x, the diagonals exactly; amax = device max|x|.
+    void apply(const float* x, float* y, const float* amax, cudaStream_t st);
+};
+
+}  // namespace kpm

@@ -74,7 +74,11 @@ size_t estimate_bytes(int n, int na, int nb, int ncol, kpm_precision prec) {
     size_t esz = prec == KPM_FP64 ? 8 : 4;
     size_t v = (size_t)dim * esz * 3 * ncol + (size_t)dim * 8;
     if (prec == KPM_FP32) v += (size_t)dim * 8;
-    if (prec == KPM_MIXED || prec == KPM_MIXED_BF16) v += (size_t)dim * 8;
+    if (prec == KPM_MIXED || prec == KPM_MIXED_BF16) {
+        // split FP16 copies of x and x^T, dense split string Hamiltonians
+        v += (size_t)dim * 8 + (size_t)4 * sa * ((sa + 7) / 8 * 8);
+        if (na != nb) v += (size_t)4 * sb * ((sb + 7) / 8 * 8);
+    }
     auto tables = [&](int m, int64_t ns) {
         int64_t nexc = m * (n - m + 1);
         int64_t nnbr = 1 + (int64_t)m * (n - m) + binom(m, 2) * binom(n - m, 2);

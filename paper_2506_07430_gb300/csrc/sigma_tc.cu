@@ -1,40 +1,33 @@
-// sigma = H x with the two-electron contraction on tcgen05 tensor cores.
+// sigma = H x on tcgen05 tensor cores (KPM_MIXED, KPM_MIXED_BF16).
 //
-// Formulation.  With E_pq = E^a_pq + E^b_pq and k_pq = h_pq - 1/2 sum_r (pr|rq),
-// the paper's second-quantized H (Methods) is
-//   H = sum_pq k_pq E_pq + 1/2 sum_{pq,rs} (pq|rs) E_pq E_rs
-//     = [k E^b + 1/2 V E^b E^b + V E^a E^b] + [k E^a + 1/2 V E^a E^a],
-// using that alpha and beta excitations commute and (pq|rs) = (rs|pq).
-// Because (pq|rs) = (qp|rs) = (pq|sr), every sum over ordered pairs folds onto
-// the NS = n(n+1)/2 unordered pairs {p,q} ("slots").
-//
-// Row pass (rows = strings of the outer index R, columns = strings C; the
-// vector is X[R][C]).  For one row R and a tile of 128 columns J:
-//   A[J][s] = sum_{e in tab(R), slot(e)=s} sgn_e X[tgt_e, J]          (opposite spin)
-//           + 1/2 sum_{f in tab(J), slot(f)=s} sgn_f X[R, tgt_f]      (same spin, C side)
-//   A[J][NS] = X[R, J]                                              (one-body)
-//   G = A W,  W[s][s'] = (pq|rs) for s, s' < NS,  W[NS][s'] = k_{s'}
-//   sigma[R, tgt_f] += sgn_f G[J][slot(f)]   for every f in tab(J)  (scatter)
+// With the alpha/beta string factorisation of the paper's second-quantized H
+// (Methods),
+//   H = F_a (x) 1 + 1 (x) F_b + sum_{pq,rs} (pq|rs) E^a_pq E^b_rs,
+// where F_s is one spin's string Hamiltonian (tables.cu).  The same-spin parts
+// are dense GEMMs with F_a, F_b (gemm_tc.cu).  This file holds the
+// opposite-spin part.  Because (pq|rs) = (qp|rs) = (pq|sr), sums over ordered
+// pairs fold onto the NS = n(n+1)/2 unordered pairs ("slots").  For one alpha
+// string R (a row of X[R][C]) and a tile of 128 beta strings J:
+//   A[J][s] = sum_{e in tab(R), slot(e) = s} sgn_e X[tgt_e, J]      (gather along rows)
+//   G = A W,  W[s][s'] = (pq|rs)
+//   sigma[R, tgt_f] += sgn_f G[J][slot(f)]   for every f in tab(J)   (scatter)
 // (<I|E_pq|J> = <J|E_qp|I> turns the outer excitation into a scatter from J.)
-// The first pass runs on X with R = alpha, C = beta and the opposite-spin part
-// on; the second on X^T with R = beta, C = alpha and the opposite-spin part
-// off; sigma = pass1 + (pass2)^T.  Every slot appears at most once in each
-// string's table, so A has at most two terms per entry.
 //
-// GEMM on the tensor cores: M = 128 columns J, N = K = P = NS+1 rounded up to a
-// multiple of 16.  A is written by the CUDA cores straight into tensor memory
-// (tcgen05.st, one TMEM lane per row J); W lives in shared memory (canonical
-// K-major layout without swizzle); D accumulates in tensor memory in FP32.
-// Operands are split into two 16-bit parts, x = hi + lo, and three MMAs
-// (A_hi W_hi + A_lo W_hi + A_hi W_lo) keep about 16 significant bits.
-// The epilogue reads D (tcgen05.ld) and scatters into the row's sigma held in
-// shared memory (shared-memory atomics), so nothing of G leaves the chip.
+// GEMM: M = 128 columns J, N = K = P = NS + 1 rounded up to 16.  A is written by
+// the CUDA cores straight into tensor memory (tcgen05.st, one TMEM lane per
+// column J); W sits in shared memory (canonical K-major layout without
+// swizzle); D accumulates in tensor memory in FP32.  Operands are split into
+// 16-bit pieces (FP16 with power-of-two scales: x in 2, W in 3 pieces, 4 MMAs;
+// or BF16 2 + 2, 3 MMAs).  The epilogue reads D (tcgen05.ld) and scatters into
+// the row's sigma in shared memory with 32-bit fixed-point integer atomics
+// (order-independent, so the result is reproducible bit for bit).
 //
-// One CTA (256 threads) per SM, persistent over rows.  Warps w and w+4 share
-// TMEM lane quadrant w%4 (rows 32(w%4)..+31) and split the slots in halves.
-// A is double-buffered in TMEM so that building the A of tile t+1 overlaps the
-// MMAs of tile t.  Waits on the MMA-completion mbarrier are bounded (about one
-// second); on expiry the kernel records an error, frees its TMEM and returns.
+// One CTA (16 warps) per SM, persistent over rows; the 4 warps of each TMEM lane
+// quadrant take 8-slot chunks round-robin.  Per tile t the CTA waits for MMA(t),
+// copies D(t) to registers, issues MMA(t+1), builds A(t+2) and scatters D(t),
+// so the tensor core runs while the CUDA cores build and scatter.  Waits on the
+// MMA-completion mbarrier are bounded (about two seconds); on expiry the kernel
+// records an error, frees its TMEM and returns.
 #include "sigma_tc.cuh"
 
 #include <cuda_bf16.h>
@@ -207,8 +200,7 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
     const int NS = p.NS;
     const int64_t Nc = p.Nc;
     uint8_t* sB = smem;
-    float* xrow = reinterpret_cast<float*>(smem + 2 * NW * P * P);   // Nc + 1 (zero pad)
-    int* srow = reinterpret_cast<int*>(xrow + (Nc + 1));             // Nc + 1, fixed point
+    int* srow = reinterpret_cast<int*>(smem + 2 * NW * P * P);       // Nc + 1, fixed point
     float* ma = reinterpret_cast<float*>(srow + (Nc + 1));           // [P] opposite-spin / identity multiplier
     int32_t* rj = reinterpret_cast<int32_t*>(ma + P);                // [P] source row of that term
     uintptr_t tail = (reinterpret_cast<uintptr_t>(rj + P) + 15) & ~uintptr_t(15);
@@ -264,7 +256,6 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
             fx = ldexpf(1.f, 31 - max(f, -90));
         }
     }
-    const float half_sa = 0.5f * sa;
     const float unscale = fx / (sa * p.wscale);   // D -> fixed point
     const float inv_fx = 1.f / fx;
     const uint32_t absent = (uint32_t)Nc;
@@ -281,8 +272,6 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
             const int c = wq + 4 * k;
             if (c < NCH) {
                 const int s0 = c * 8;
-                const uint4 w4 = __ldg(p.tslot8 + (int64_t)c * Nc + jcc);
-                const uint32_t w[4] = {w4.x, w4.y, w4.z, w4.w};
                 float xa[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
@@ -294,12 +283,7 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
                 for (int u = 0; u < 8; u += 2) {
                     float v[2];
 #pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const uint32_t e = (w[(u + q) >> 1] >> (16 * ((u + q) & 1))) & 0xFFFFu;
-                        const float xb = xrow[e & 0x7FFFu];
-                        const float sb = __uint_as_float(__float_as_uint(xb) ^ ((e & 0x8000u) << 16));
-                        v[q] = valid ? fmaf(half_sa, sb, xa[u + q]) : 0.f;
-                    }
+                    for (int q = 0; q < 2; ++q) v[q] = valid ? xa[u + q] : 0.f;
                     const float h0 = round16<FP16>(v[0]), h1 = round16<FP16>(v[1]);
                     hi[u / 2] = pack2<FP16>(h0, h1);
                     lo[u / 2] = pack2<FP16>(v[0] - h0, v[1] - h1);
@@ -379,16 +363,9 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
     };
 
     for (int64_t ir = blockIdx.x; ir < p.Nr; ir += gridDim.x) {
-        for (int64_t j = tid; j < Nc; j += RP_THREADS) {
-            xrow[j] = p.X[ir * Nc + j];
-            srow[j] = 0;
-        }
-        if (tid == 0) {
-            xrow[Nc] = 0.f;
-            srow[Nc] = 0;
-        }
+        for (int64_t j = tid; j <= Nc; j += RP_THREADS) srow[j] = 0;
         for (int s = tid; s < P; s += RP_THREADS) {
-            ma[s] = (s == NS) ? sa : 0.f;   // identity column: X[R, J] itself (one-body k row)
+            ma[s] = 0.f;
             rj[s] = (int32_t)ir;
         }
         __syncthreads();
@@ -470,10 +447,6 @@ __global__ void k_wimg(const double* __restrict__ h1, const double* __restrict__
             int pi, qi;
             slot_pair(kc, pi, qi);
             w = eri[(((int64_t)pi * n + qi) * n + po) * n + qo];
-        } else if (kc == NS) {
-            double k = h1[po * n + qo];
-            for (int r = 0; r < n; ++r) k -= 0.5 * eri[(((int64_t)po * n + r) * n + r) * n + qo];
-            w = k;
         }
     }
     w *= wscale;
@@ -520,38 +493,6 @@ __global__ void k_slot_table(const int32_t* __restrict__ tgt, const uint16_t* __
         (uint16_t)(tgt[i] | (sgn[i] < 0 ? 0x8000 : 0));
 }
 
-// out[c][r] = in[r][c] for an R x C matrix.
-__global__ void k_transpose(const float* __restrict__ in, float* __restrict__ out, int64_t R,
-                            int64_t C) {
-    __shared__ float t[32][33];
-    const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        int64_t r = r0 + k, c = c0 + threadIdx.x;
-        if (r < R && c < C) t[k][threadIdx.x] = in[r * C + c];
-    }
-    __syncthreads();
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        int64_t c = c0 + k, r = r0 + threadIdx.x;
-        if (r < R && c < C) out[c * R + r] = t[threadIdx.x][k];
-    }
-}
-
-// y[r][c] += sp[c][r] for an R x C matrix y.
-__global__ void k_add_transposed(float* __restrict__ y, const float* __restrict__ sp, int64_t R,
-                                 int64_t C) {
-    __shared__ float t[32][33];
-    const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        int64_t c = c0 + k, r = r0 + threadIdx.x;
-        if (r < R && c < C) t[k][threadIdx.x] = sp[c * R + r];
-    }
-    __syncthreads();
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        int64_t r = r0 + k, c = c0 + threadIdx.x;
-        if (r < R && c < C) y[r * C + c] += t[threadIdx.x][k];
-    }
-}
-
 uint32_t tmem_cols(int P) {
     uint32_t need = (uint32_t)(3 * P), c = 32;
     while (c < need) c <<= 1;
@@ -559,7 +500,7 @@ uint32_t tmem_cols(int P) {
 }
 
 size_t rowpass_smem(int P, int NW, int64_t Nc) {
-    return (size_t)2 * NW * P * P + 8 * (size_t)(Nc + 1) + 8 * (size_t)P + 64;
+    return (size_t)2 * NW * P * P + 4 * (size_t)(Nc + 1) + 8 * (size_t)P + 64;
 }
 
 template <int P>
@@ -649,13 +590,11 @@ void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
             KPM_LAUNCHED();
         }
     };
-    build_slots(A, slot_a);
     build_slots(B, slot_b);
-    xt.alloc((size_t)dim * sizeof(float));
-    sp.alloc((size_t)dim * sizeof(float));
     err.alloc(sizeof(int));
     amax.alloc(2 * sizeof(unsigned));
     KPM_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+    dense.init(A, B, &A == &B, err.as<int>(), st);
 }
 
 void TcSigma::apply(const float* x, float* y, int ncol, cudaStream_t st) {
@@ -663,13 +602,12 @@ void TcSigma::apply(const float* x, float* y, int ncol, cudaStream_t st) {
     for (int c = 0; c < ncol; ++c) {
         const float* X = x + (size_t)c * dim;
         float* Y = y + (size_t)c * dim;
-        // max|x|: FP16 operand scale and fixed-point range; both passes read the
-        // same numbers (x and its transpose)
+        // max|x|: FP16 operand scales and the fixed-point range of the scatter
         KPM_CUDA(cudaMemsetAsync(amax.p, 0, sizeof(unsigned), st));
         k_absmax<<<1024, 256, 0, st>>>(X, dim, amax.as<unsigned>());
         KPM_LAUNCHED();
         const float* am = reinterpret_cast<const float*>(amax.p);
-        // pass 1: rows alpha, columns beta, opposite-spin part on
+        // opposite-spin part: rows alpha, columns beta; writes Y
         RowPass p1{X, Y, nsa, nsb, slot_b.as<uint4>(),
                    ta->tgt.as<int32_t>(), ta->pq.as<uint16_t>(), ta->sgn.as<int8_t>(), ta->nexc,
                    wimg.as<uint4>(), NS, n, nc, am, wscale, gbound, tb->nexc, err.as<int>()};
@@ -677,20 +615,8 @@ void TcSigma::apply(const float* x, float* y, int ncol, cudaStream_t st) {
         void* args1[] = {&p1};
         KPM_CUDA(cudaLaunchKernel(kernel, dim3(g1), dim3(RP_THREADS), args1, smem_bytes, st));
         KPM_LAUNCHED();
-        // pass 2 on x^T: rows beta, columns alpha, same-spin alpha part only
-        dim3 tb2(32, 8);
-        dim3 gt((unsigned)((nsb + 31) / 32), (unsigned)((nsa + 31) / 32));
-        k_transpose<<<gt, tb2, 0, st>>>(X, xt.as<float>(), nsa, nsb);
-        KPM_LAUNCHED();
-        RowPass p2{xt.as<float>(), sp.as<float>(), nsb, nsa, slot_a.as<uint4>(),
-                   nullptr, nullptr, nullptr, 0, wimg.as<uint4>(),
-                   NS, n, nc, am, wscale, gbound, ta->nexc, err.as<int>()};
-        int g2 = (int)(nsb < nsm ? nsb : nsm);
-        void* args2[] = {&p2};
-        KPM_CUDA(cudaLaunchKernel(kernel, dim3(g2), dim3(RP_THREADS), args2, smem_bytes, st));
-        KPM_LAUNCHED();
-        k_add_transposed<<<gt, tb2, 0, st>>>(Y, sp.as<float>(), nsa, nsb);
-        KPM_LAUNCHED();
+        // same-spin parts (dense GEMMs) and the exact diagonal, added into Y
+        dense.apply(X, Y, am, st);
     }
 }
 

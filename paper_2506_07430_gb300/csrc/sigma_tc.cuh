@@ -1,6 +1,7 @@
 // Tensor-core (tcgen05) sigma for KPM_MIXED contexts.
 #pragma once
 #include "common.cuh"
+#include "gemm_tc.cuh"
 
 namespace kpm {
 
@@ -17,9 +18,9 @@ struct TcSigma {
     void* kernel = nullptr;       // k_rowpass instantiation for P
     const SpinTables* ta = nullptr;
     const SpinTables* tb = nullptr;
-    DevBuf wimg;                  // W = [(pq|rs) ; k] as split 16-bit operand image (hi | lo)
-    DevBuf slot_a, slot_b;        // uint16 [P/8][N_s][8] pair-slot -> target | sign << 15 (N_s: none)
-    DevBuf xt, sp;                // workspaces: x transposed, transposed-pass output
+    DevBuf wimg;                  // W = (pq|rs) over slots as split 16-bit operand image
+    DevBuf slot_b;                // uint16 [P/8][N_b][8] pair-slot -> target | sign << 15 (N_b: none)
+    DenseSS dense;                // same-spin parts (dense GEMMs with F_a, F_b)
     DevBuf err;                   // int error flag (1: a bounded wait ran out)
     DevBuf amax;                  // max |x| (float bits): operand scale, fixed-point range
     size_t smem_bytes = 0;
