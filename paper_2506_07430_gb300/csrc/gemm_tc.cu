@@ -158,7 +158,16 @@ k_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensor
     int* consumed = issued + 1;       // stages whose full barrier the MMA thread passed
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.x * GM_BM, n0 = blockIdx.y * GM_BN;
+    // grouped rasterisation: groups of GROUP_M row tiles walk all column tiles,
+    // so the group's A panels and the current B panels stay in L2
+    constexpr int GROUP_M = 16;
+    const int nM = (g.M + GM_BM - 1) / GM_BM, nN = (g.N + GM_BN - 1) / GM_BN;
+    const int b = blockIdx.x;
+    const int gsize = GROUP_M * nN;
+    const int first_m = (b / gsize) * GROUP_M;
+    const int gm = min(nM - first_m, GROUP_M);
+    const int m0 = (first_m + (b % gsize) % gm) * GM_BM;
+    const int n0 = ((b % gsize) / gm) * GM_BN;
     const int nk = (g.K + GM_BK - 1) / GM_BK;
 
     if (tid == 0) {
@@ -506,7 +515,7 @@ void DenseSS::apply(const float* x, float* y, const float* amax, cudaStream_t st
         CUtensorMap b1 = make_map(xl.as<__half>(), na, nb, pb, GM_BN);
         GemmArgs g{(int)nb, (int)na, (int)nb, y, nb, 1.0f, amax, (float)wscale_b,
                    nullptr, nullptr, nullptr, err};
-        dim3 grid((unsigned)((nb + GM_BM - 1) / GM_BM), (unsigned)((na + GM_BN - 1) / GM_BN));
+        dim3 grid((unsigned)(((nb + GM_BM - 1) / GM_BM) * ((na + GM_BN - 1) / GM_BN)));
         k_gemm<<<grid, GM_THREADS, smem, st>>>(a0, a1, b0, b1, g);
         KPM_LAUNCHED();
     }
@@ -518,7 +527,7 @@ void DenseSS::apply(const float* x, float* y, const float* amax, cudaStream_t st
         CUtensorMap b1 = make_map(fa_lo->as<__half>(), na, na, pa, GM_BN);
         GemmArgs g{(int)nb, (int)na, (int)na, y, nb, 1.0f, amax, (float)wscale_a,
                    x, db.as<float2>(), da->as<float2>(), err};
-        dim3 grid((unsigned)((nb + GM_BM - 1) / GM_BM), (unsigned)((na + GM_BN - 1) / GM_BN));
+        dim3 grid((unsigned)(((nb + GM_BM - 1) / GM_BM) * ((na + GM_BN - 1) / GM_BN)));
         k_gemm<<<grid, GM_THREADS, smem, st>>>(a0, a1, b0, b1, g);
         KPM_LAUNCHED();
     }

@@ -6,24 +6,28 @@
 // where F_s is one spin's string Hamiltonian (tables.cu).  The same-spin parts
 // are dense GEMMs with F_a, F_b (gemm_tc.cu).  This file holds the
 // opposite-spin part.  Because (pq|rs) = (qp|rs) = (pq|sr), sums over ordered
-// pairs fold onto the NS = n(n+1)/2 unordered pairs ("slots").  For one alpha
-// string R (a row of X[R][C]) and a tile of 128 beta strings J:
-//   A[J][s] = sum_{e in tab(R), slot(e) = s} sgn_e X[tgt_e, J]      (gather along rows)
-//   G = A W,  W[s][s'] = (pq|rs)
-//   sigma[R, tgt_f] += sgn_f G[J][slot(f)]   for every f in tab(J)   (scatter)
+// pairs fold onto the NS = n(n+1)/2 unordered pairs ("slots"); a string has at
+// most one table entry per slot.  For one alpha string R (a row of X[R][C]) and
+// a tile of 128 beta strings J:
+//   A[J][e] = X[tgt_e, J]                    for the entries e of tab(R)  (gather)
+//   B_R[s][e] = sgn_e W[slot(e)][s],         W[s][s'] = (pq|rs)
+//   G = A B_R^T
+//   sigma[R, tgt_f] += sgn_f G[J][slot(f)]   for every f in tab(J)        (scatter)
 // (<I|E_pq|J> = <J|E_qp|I> turns the outer excitation into a scatter from J.)
 //
-// GEMM: M = 128 columns J, N = K = P = NS + 1 rounded up to 16.  A is written by
-// the CUDA cores straight into tensor memory (tcgen05.st, one TMEM lane per
-// column J); W sits in shared memory (canonical K-major layout without
-// swizzle); D accumulates in tensor memory in FP32.  Operands are split into
-// 16-bit pieces (FP16 with power-of-two scales: x in 2, W in 3 pieces, 4 MMAs;
-// or BF16 2 + 2, 3 MMAs).  The epilogue reads D (tcgen05.ld) and scatters into
-// the row's sigma in shared memory with 32-bit fixed-point integer atomics
-// (order-independent, so the result is reproducible bit for bit).
+// GEMM per tile: M = 128 columns J, K = KR (the row's nexc entries rounded up
+// to 16), N = P (NS + 1 rounded up to 16).  A is written by the CUDA cores
+// straight into tensor memory (tcgen05.st, one TMEM lane per column J); B_R is
+// gathered once per row from the W image into shared memory (canonical K-major
+// layout without swizzle, signs folded in); D accumulates in tensor memory in
+// FP32.  Operands are split into 16-bit pieces (FP16 with power-of-two scales:
+// x in 2, W in 3 pieces, 4 MMAs; or BF16 2 + 2, 3 MMAs).  The epilogue reads D
+// (tcgen05.ld) and scatters into the row's sigma in shared memory with 32-bit
+// fixed-point integer atomics (order-independent, so the result is
+// reproducible bit for bit).
 //
 // One CTA (16 warps) per SM, persistent over rows; the 4 warps of each TMEM lane
-// quadrant take 8-slot chunks round-robin.  Per tile t the CTA waits for MMA(t),
+// quadrant take chunks of 8 (entries or slots) round-robin.  Per tile t the CTA waits for MMA(t),
 // copies D(t) to registers, issues MMA(t+1), builds A(t+2) and scatters D(t),
 // so the tensor core runs while the CUDA cores build and scatter.  Waits on the
 // MMA-completion mbarrier are bounded (about two seconds); on expiry the kernel
@@ -115,6 +119,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t parity) {
     return ok != 0;
 }
 
+// 4-byte asynchronous global -> shared copy; src_bytes = 0 writes zero
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src),
+                 "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Shared-memory matrix descriptor, canonical K-major layout without swizzle:
 // 8-row x 16-byte core matrices; LBO = byte distance between core matrices
 // adjacent along K, SBO = between core matrices adjacent along M/N.
@@ -165,11 +182,12 @@ struct RowPass {
     const uint4* tslot8;     // [P/8][Nc]: 8 16-bit entries per chunk of 8 slots (slot 8c+u in
                              // half u of the 128-bit word): target string | sign << 15,
                              // Nc when the slot is absent
-    const int32_t* rtgt;     // [Nr][rnexc] row-string tables (opposite-spin part)
+    const int32_t* rtgt;     // [Nr][rnexc] row-string tables
     const uint16_t* rpq;
     const int8_t* rsgn;
-    int rnexc;               // 0: opposite-spin part off
-    const uint4* wimg;       // W image: NW pieces of 2 P^2 bytes each
+    int rnexc;               // table entries per row string (K of the row's GEMM)
+    int KR;                  // rnexc rounded up to 16
+    const __half* wrow;      // W by input slot: NW pieces of [P][P] 16-bit (bits of the format)
     int NS, n;
     uint32_t ncols;          // TMEM columns allocated
     const float* amax;       // device max|X| (operand scaling and fixed-point range)
@@ -181,29 +199,37 @@ struct RowPass {
 
 constexpr int RP_WARPS = 16;                 // 4 warps per TMEM lane quadrant
 constexpr int RP_THREADS = 32 * RP_WARPS;
+constexpr int RP_MAXK = 96;                  // largest KR: 9 * 10 = 90 entries rounded up
 
-// P: padded K = N (multiple of 16); FP16: operand format (else BF16);
-// NW: number of 16-bit pieces of W (2 or 3).  MMA passes: A_hi W_j for every
-// piece j, plus A_lo W_0.
+// P: padded N (multiple of 16); FP16: operand format (else BF16); NW: pieces of W.
+// Per row R the K dimension holds R's own table entries e (KR = rnexc rounded up
+// to 16): A[J][e] = X[tgt_e, J], and the row's B, B_R[s][e] = sgn_e W[slot(e)][s],
+// is gathered from the W image into shared memory (canonical K-major layout
+// without swizzle).  MMA passes: A_hi B_j for every piece j, plus A_lo B_0.
 //
-// Work split: the P slots form P/8 chunks of 8; the 4 warps of a lane quadrant
-// take the chunks round-robin (chunk c -> warp c % 4 of the quadrant).  Per
-// tile t the CTA (i) waits for MMA(t), (ii) copies D(t) into registers, (iii)
-// issues MMA(t+1), (iv) builds A(t+2) into the buffer MMA(t) has finished with,
-// and (v) scatters D(t) from registers; so the tensor core runs while the CUDA
-// cores build and scatter.
+// Work split: the KR entries form KR/8 chunks of 8 (A build) and the P output
+// slots P/8 chunks (scatter); the 4 warps of a lane quadrant take chunks
+// round-robin.  Per tile t the CTA waits for MMA(t), copies D(t) into
+// registers, issues MMA(t+1), builds A(t+2) into the buffer MMA(t) has finished
+// with, starts the asynchronous gather copies of tile t+3 into shared memory
+// and scatters D(t).  The gather of a tile is thus in flight for a whole
+// iteration, and the scatter's table words, loaded at the start of the
+// iteration, arrive during the build.
 template <int P, bool FP16, int NW>
 __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
-    constexpr int NCH = P / 8;                     // 8-slot chunks
-    constexpr int MAXC = (NCH + 3) / 4;            // chunks per warp (upper bound)
+    constexpr int NCH = P / 8;                     // output chunks of 8 slots
+    constexpr int MAXC = (NCH + 3) / 4;            // output chunks per warp (upper bound)
+    constexpr int MAXA = (RP_MAXK / 8 + 3) / 4;    // input chunks per warp (upper bound)
     extern __shared__ __align__(1024) unsigned char smem[];
-    const int NS = p.NS;
+    const int KR = p.KR;
     const int64_t Nc = p.Nc;
-    uint8_t* sB = smem;
-    int* srow = reinterpret_cast<int*>(smem + 2 * NW * P * P);       // Nc + 1, fixed point
-    float* ma = reinterpret_cast<float*>(srow + (Nc + 1));           // [P] opposite-spin / identity multiplier
-    int32_t* rj = reinterpret_cast<int32_t*>(ma + P);                // [P] source row of that term
-    uintptr_t tail = (reinterpret_cast<uintptr_t>(rj + P) + 15) & ~uintptr_t(15);
+    uint8_t* sB = smem;                                               // NW pieces of P x KR
+    const uint32_t piece_bytes = (uint32_t)(P * KR * 2);
+    int* srow = reinterpret_cast<int*>(smem + NW * piece_bytes);      // Nc + 1, fixed point
+    int32_t* rje = srow + (Nc + 1);                                   // [RP_MAXK] source rows
+    float* sX = reinterpret_cast<float*>(
+        (reinterpret_cast<uintptr_t>(rje + RP_MAXK) + 15) & ~uintptr_t(15));  // [2][KR][128]
+    uintptr_t tail = reinterpret_cast<uintptr_t>(sX + 2 * KR * 128);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(tail);
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(mbar + 1);
     int* abort_flag = reinterpret_cast<int*>(tmem_holder + 1);
@@ -213,11 +239,6 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
     const int quad = warp & 3, wq = warp >> 2;
     const int m = quad * 32 + lane;
 
-    {
-        constexpr int nv = (2 * NW * P * P) / 16;
-        uint4* dst = reinterpret_cast<uint4*>(sB);
-        for (int i = tid; i < nv; i += RP_THREADS) dst[i] = p.wimg[i];
-    }
     if (tid == 0) {
         mbar_init(mbar, 1);
         *abort_flag = 0;
@@ -227,7 +248,6 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
         tmem_alloc(tmem_holder, p.ncols);
         tmem_relinquish();
     }
-    fence_proxy_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -235,22 +255,19 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
     const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
     constexpr uint32_t idesc = instr_desc(128, P, !FP16);
     const uint32_t sB_addr = smem_u32(sB);
-    constexpr uint32_t SBO = 16u * P, LBO = 128u;
+    const uint32_t sX_addr = smem_u32(sX);
+    const uint32_t SBO = 16u * (uint32_t)KR, LBO = 128u;
     const int ntiles = (int)((Nc + 127) / 128);
-    // Operand scale (FP16): A entries stay below 1.5 * 2^14.  Fixed point for the
-    // scattered sums: every target receives nexc_c terms of magnitude at most
-    // |G| <= 1.5 max|x| gbound, so with fx = 2^f and
-    // fx * 1.02 * nexc_c * 1.5 * max|x| * gbound < 2^31 no partial sum overflows.
-    // Integer addition is associative: the sums do not depend on the order of the
-    // atomics.
+    const int nchA = KR / 8;
     float sa = 1.f, fx = 1.f;
     {
         const float mx = *p.amax;
         if (mx > 0.f && isfinite(mx)) {
             int e;
-            frexpf(mx, &e);  // mx < 2^e
+            frexpf(mx, &e);  // mx < 2^e; A entries are single values of x
             if (FP16) sa = ldexpf(1.f, 14 - max(e, -90));
-            const float bound = 1.02f * (float)p.nexc_c * 1.5f * mx * p.gbound;
+            // every target receives nexc_c terms of magnitude <= max|x| gbound
+            const float bound = 1.02f * (float)p.nexc_c * mx * p.gbound;
             int f = -90;
             if (bound > 0.f) frexpf(bound, &f);  // bound < 2^f
             fx = ldexpf(1.f, 31 - max(f, -90));
@@ -261,34 +278,48 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
     const uint32_t absent = (uint32_t)Nc;
     uint32_t phase = 0;
 
-    auto build = [&](int t, int buf) {
+    // stage the gather X[tgt_e, J] of tile t for this thread's entry chunks
+    // (4-byte cp.async: rows of X are not 16-byte aligned in general)
+    auto copies = [&](int t) {
         const int64_t jc = (int64_t)t * 128 + m;
         const bool valid = jc < Nc;
-        const int64_t jcc = valid ? jc : Nc - 1;  // clamped address for the tail tile
-        const uint32_t a_hi = tbase + lane_base + (uint32_t)(buf * P);
-        const uint32_t a_lo = a_hi + (uint32_t)(P / 2);
+        const uint32_t dst0 = sX_addr + (uint32_t)((t & 1) * KR) * 512u + (uint32_t)m * 4u;
 #pragma unroll
-        for (int k = 0; k < MAXC; ++k) {
+        for (int k = 0; k < MAXA; ++k) {
             const int c = wq + 4 * k;
-            if (c < NCH) {
-                const int s0 = c * 8;
-                float xa[8];
+            if (c < nchA) {
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                    const float mult = ma[s0 + u];
-                    xa[u] = (mult != 0.f) ? mult * __ldg(p.X + (int64_t)rj[s0 + u] * Nc + jcc) : 0.f;
+                    const int e = c * 8 + u;
+                    const int r = rje[e];
+                    const bool ok = valid && r >= 0;
+                    const float* src = ok ? p.X + (int64_t)r * Nc + jc : p.X;
+                    cp_async4(dst0 + (uint32_t)e * 512u, src, ok ? 4u : 0u);
                 }
+            }
+        }
+        cp_async_commit();
+    };
+
+    // A(t) = split X gather of tile t (staged by copies(t)) -> TMEM buffer buf
+    auto build = [&](int t, int buf) {
+        const float* xs = sX + (size_t)((t & 1) * KR) * 128 + m;
+        const uint32_t a_hi = tbase + lane_base + (uint32_t)(buf * KR);
+        const uint32_t a_lo = a_hi + (uint32_t)(KR / 2);
+#pragma unroll
+        for (int k = 0; k < MAXA; ++k) {
+            const int c = wq + 4 * k;
+            if (c < nchA) {
                 uint32_t hi[4], lo[4];
 #pragma unroll
                 for (int u = 0; u < 8; u += 2) {
-                    float v[2];
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) v[q] = valid ? xa[u + q] : 0.f;
-                    const float h0 = round16<FP16>(v[0]), h1 = round16<FP16>(v[1]);
+                    const float v0 = xs[(c * 8 + u) * 128] * sa;
+                    const float v1 = xs[(c * 8 + u + 1) * 128] * sa;
+                    const float h0 = round16<FP16>(v0), h1 = round16<FP16>(v1);
                     hi[u / 2] = pack2<FP16>(h0, h1);
-                    lo[u / 2] = pack2<FP16>(v[0] - h0, v[1] - h1);
+                    lo[u / 2] = pack2<FP16>(v0 - h0, v1 - h1);
                 }
-                const uint32_t col = (uint32_t)(s0 / 2);
+                const uint32_t col = (uint32_t)(c * 4);
                 tmem_st4(a_hi + col, hi[0], hi[1], hi[2], hi[3]);
                 tmem_st4(a_lo + col, lo[0], lo[1], lo[2], lo[3]);
             }
@@ -297,17 +328,16 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
 
     auto issue = [&](int t) {
         const int buf = t & 1;
-        const uint32_t a_hi = tbase + (uint32_t)(buf * P);
-        const uint32_t a_lo = a_hi + (uint32_t)(P / 2);
-        const uint32_t d = tbase + (uint32_t)(2 * P);
-        constexpr int ksteps = P / 16;
+        const uint32_t a_hi = tbase + (uint32_t)(buf * KR);
+        const uint32_t a_lo = a_hi + (uint32_t)(KR / 2);
+        const uint32_t d = tbase + (uint32_t)(2 * KR);
+        const int ksteps = KR / 16;
 #pragma unroll
         for (int pass = 0; pass < NW + 1; ++pass) {
             // pass 0: A_hi W_0, pass 1: A_lo W_0, pass j+1 (j >= 1): A_hi W_j
             const uint32_t a = (pass == 1) ? a_lo : a_hi;
             const int piece = pass <= 1 ? 0 : pass - 1;
-            const uint32_t bbase = sB_addr + (uint32_t)(piece * 2 * P * P);
-#pragma unroll
+            const uint32_t bbase = sB_addr + (uint32_t)piece * piece_bytes;
             for (int j = 0; j < ksteps; ++j) {
                 uint64_t bd = smem_desc(bbase + (uint32_t)(j * 256), LBO, SBO);
                 mma_ts(d, a + (uint32_t)(j * 8), bd, idesc, (pass | j) != 0);
@@ -316,9 +346,8 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
         mma_commit(mbar);
     };
 
-    // D(t) of this thread's row and this warp's chunks -> registers
     auto load_d = [&](uint32_t (&dr)[MAXC][8]) {
-        const uint32_t dcol = tbase + lane_base + (uint32_t)(2 * P);
+        const uint32_t dcol = tbase + lane_base + (uint32_t)(2 * KR);
 #pragma unroll
         for (int k = 0; k < MAXC; ++k) {
             const int c = wq + 4 * k;
@@ -327,16 +356,23 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
         tmem_ld_wait();
     };
 
-    auto scatter = [&](int t, const uint32_t (&dr)[MAXC][8]) {
+    auto load_words = [&](int t, uint4 (&w4)[MAXC]) {
         const int64_t jc = (int64_t)t * 128 + m;
-        const bool valid = jc < Nc;
-        const int64_t jcc = valid ? jc : Nc - 1;
+        const int64_t jcc = jc < Nc ? jc : Nc - 1;
+#pragma unroll
+        for (int k = 0; k < MAXC; ++k) {
+            const int c = wq + 4 * k;
+            if (c < NCH) w4[k] = __ldg(p.tslot8 + (int64_t)c * Nc + jcc);
+        }
+    };
+
+    auto scatter = [&](int t, const uint32_t (&dr)[MAXC][8], const uint4 (&w4)[MAXC]) {
+        const bool valid = (int64_t)t * 128 + m < Nc;
 #pragma unroll
         for (int k = 0; k < MAXC; ++k) {
             const int c = wq + 4 * k;
             if (c < NCH) {
-                const uint4 w4 = __ldg(p.tslot8 + (int64_t)c * Nc + jcc);
-                const uint32_t w[4] = {w4.x, w4.y, w4.z, w4.w};
+                const uint32_t w[4] = {w4[k].x, w4[k].y, w4[k].z, w4[k].w};
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const uint32_t e = (w[u >> 1] >> (16 * (u & 1))) & 0xFFFFu;
@@ -363,22 +399,40 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
     };
 
     for (int64_t ir = blockIdx.x; ir < p.Nr; ir += gridDim.x) {
+        // row set-up: zero sigma, the row's source rows, and its B (signs folded in)
         for (int64_t j = tid; j <= Nc; j += RP_THREADS) srow[j] = 0;
-        for (int s = tid; s < P; s += RP_THREADS) {
-            ma[s] = 0.f;
-            rj[s] = (int32_t)ir;
+        for (int e = tid; e < RP_MAXK; e += RP_THREADS)
+            rje[e] = e < p.rnexc ? p.rtgt[ir * p.rnexc + e] : -1;
+        {
+            const uint16_t* wsrc = reinterpret_cast<const uint16_t*>(p.wrow);
+            const int tot = NW * P * KR;
+            for (int i = tid; i < tot; i += RP_THREADS) {
+                const int piece = i / (P * KR);
+                const int rem = i % (P * KR);
+                const int e = rem / P, nn = rem % P;   // consecutive threads: consecutive nn
+                uint16_t v = 0;
+                if (e < p.rnexc) {
+                    const int g = p.rpq[ir * p.rnexc + e];
+                    int a = g / p.n, b = g % p.n;
+                    if (a > b) { int t = a; a = b; b = t; }
+                    const int sl = b * (b + 1) / 2 + a;
+                    v = wsrc[((size_t)piece * P + sl) * P + nn];
+                    if (p.rsgn[ir * p.rnexc + e] < 0) v ^= 0x8000u;   // exact negation
+                }
+                const uint32_t off = (uint32_t)piece * piece_bytes + (uint32_t)(nn / 8) * SBO +
+                                     (uint32_t)(e / 8) * 128 + (uint32_t)(nn % 8) * 16 +
+                                     (uint32_t)(e % 8) * 2;
+                *reinterpret_cast<uint16_t*>(sB + off) = v;
+            }
         }
-        __syncthreads();
-        for (int e = tid; e < p.rnexc; e += RP_THREADS) {
-            const int g = p.rpq[ir * p.rnexc + e];
-            int a = g / p.n, b = g % p.n;
-            if (a > b) { int t = a; a = b; b = t; }
-            const int s = b * (b + 1) / 2 + a;
-            ma[s] = p.rsgn[ir * p.rnexc + e] < 0 ? -sa : sa;
-            rj[s] = p.rtgt[ir * p.rnexc + e];
-        }
+        fence_proxy_async_smem();
         __syncthreads();
 
+        // tiles: copies(t + 3) and build(t + 2) run while MMA(t + 1) does;
+        // stage t & 1 holds tile t's gather from copies(t) until build(t)
+        copies(0);
+        if (ntiles > 1) copies(1);
+        if (ntiles > 1) cp_async_wait<1>(); else cp_async_wait<0>();
         build(0, 0);
         tmem_st_wait();
         tc_fence_before();
@@ -387,8 +441,14 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
             tc_fence_after();
             issue(0);
         }
-        if (ntiles > 1) build(1, 1);
+        if (ntiles > 1) {
+            cp_async_wait<0>();
+            build(1, 1);
+        }
+        if (ntiles > 2) copies(2);
         for (int t = 0; t < ntiles; ++t) {
+            uint4 w4[MAXC];
+            load_words(t, w4);
             wait_mma();
             __syncthreads();
             if (*abort_flag) break;
@@ -402,9 +462,14 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
                 tc_fence_after();
                 issue(t + 1);
             }
-            if (t + 2 < ntiles) build(t + 2, t & 1);
-            scatter(t, dr);
+            if (t + 2 < ntiles) {
+                cp_async_wait<0>();
+                build(t + 2, t & 1);
+            }
+            if (t + 3 < ntiles) copies(t + 3);
+            scatter(t, dr, w4);
         }
+        cp_async_wait<0>();
         __syncthreads();
         if (*abort_flag) break;
         for (int64_t j = tid; j < Nc; j += RP_THREADS) p.Y[ir * Nc + j] = (float)srow[j] * inv_fx;
@@ -427,31 +492,23 @@ __global__ void k_absmax(const float* __restrict__ x, int64_t n, unsigned* out) 
 
 // ---------------------------------------------------------------- set-up kernels
 
-// W image: B operand of the MMA is W^T (N = output slot, K = input slot) in the
-// canonical K-major layout; element (nr, kc) at (nr/8)*16P + (kc/8)*128 +
-// (nr%8)*16 + (kc%8)*2 bytes.  W (scaled by the power of two wscale) is split
-// into NW 16-bit pieces, piece j = round(W - sum_{i<j} piece_i); piece j sits at
-// byte offset j * 2 P^2.
+// W image by input slot: NW pieces of a P x P row-major array of 16-bit values,
+// element (s_in, s_out) = piece j of W[s_in][s_out] = (pq|rs) (scaled by the
+// power of two wscale), piece j = round(W - sum_{i<j} piece_i).
 template <bool FP16>
-__global__ void k_wimg(const double* __restrict__ h1, const double* __restrict__ eri, int n,
-                       int P, int NS, int NW, uint8_t* __restrict__ img, double wscale) {
+__global__ void k_wimg(const double* __restrict__ eri, int n, int P, int NS, int NW,
+                       uint16_t* __restrict__ img, double wscale) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= P * P) return;
-    const int nr = idx / P;  // output slot
-    const int kc = idx % P;  // input slot
+    const int si = idx / P, so = idx % P;
     double w = 0.0;
-    if (nr < NS) {
-        int po, qo;
-        slot_pair(nr, po, qo);
-        if (kc < NS) {
-            int pi, qi;
-            slot_pair(kc, pi, qi);
-            w = eri[(((int64_t)pi * n + qi) * n + po) * n + qo];
-        }
+    if (si < NS && so < NS) {
+        int pi, qi, po, qo;
+        slot_pair(si, pi, qi);
+        slot_pair(so, po, qo);
+        w = eri[(((int64_t)pi * n + qi) * n + po) * n + qo];
     }
     w *= wscale;
-    const size_t off = (size_t)(nr / 8) * (16 * P) + (size_t)(kc / 8) * 128 + (nr % 8) * 16 +
-                       (kc % 8) * 2;
     double rest = w;
     for (int j = 0; j < NW; ++j) {
         uint16_t bits;
@@ -465,7 +522,7 @@ __global__ void k_wimg(const double* __restrict__ h1, const double* __restrict__
             part = (double)__bfloat162float(h);
             bits = *reinterpret_cast<uint16_t*>(&h);
         }
-        *reinterpret_cast<uint16_t*>(img + (size_t)j * 2 * P * P + off) = bits;
+        img[(size_t)j * P * P + idx] = bits;
         rest -= part;
     }
 }
@@ -493,14 +550,15 @@ __global__ void k_slot_table(const int32_t* __restrict__ tgt, const uint16_t* __
         (uint16_t)(tgt[i] | (sgn[i] < 0 ? 0x8000 : 0));
 }
 
-uint32_t tmem_cols(int P) {
-    uint32_t need = (uint32_t)(3 * P), c = 32;
+uint32_t tmem_cols(int P, int KR) {
+    uint32_t need = (uint32_t)(2 * KR + P), c = 32;
     while (c < need) c <<= 1;
     return c;
 }
 
-size_t rowpass_smem(int P, int NW, int64_t Nc) {
-    return (size_t)2 * NW * P * P + 4 * (size_t)(Nc + 1) + 8 * (size_t)P + 64;
+size_t rowpass_smem(int P, int NW, int KR, int64_t Nc) {
+    return (size_t)2 * NW * P * KR + 4 * (size_t)(Nc + 1) + 4 * RP_MAXK + 16 +
+           (size_t)2 * KR * 128 * 4 + 64;
 }
 
 template <int P>
@@ -539,7 +597,8 @@ void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
     fp16 = use_fp16;
     nw = fp16 ? 3 : 2;
     kernel = rowpass_kernel(P, fp16);
-    if (!kernel || tmem_cols(P) > 512 || A.ns > 32766 || B.ns > 32766)
+    KR = ((A.nexc + 15) / 16) * 16;
+    if (!kernel || KR > RP_MAXK || tmem_cols(P, KR) > 512 || A.ns > 32766 || B.ns > 32766)
         KPM_THROW(KPM_EUNSUPPORTED, "tensor-core sigma supports up to 16 orbitals");
     int dev = 0;
     KPM_CUDA(cudaGetDevice(&dev));
@@ -550,7 +609,7 @@ void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
     nsm = prop.multiProcessorCount;
     gbound = (float)(wcolsum * (1.0 + 1e-6));
     int64_t ncmax = nsa > nsb ? nsa : nsb;
-    smem_bytes = rowpass_smem(P, nw, ncmax);
+    smem_bytes = rowpass_smem(P, nw, KR, ncmax);
     // at least ~116 KB so that exactly one CTA (and one TMEM allocation) fits per SM
     size_t floor_bytes = 116 * 1024;
     if (smem_bytes < floor_bytes) smem_bytes = floor_bytes;
@@ -570,11 +629,11 @@ void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
     wimg.alloc(wbytes);
     KPM_CUDA(cudaMemsetAsync(wimg.p, 0, wbytes, st));
     if (fp16)
-        k_wimg<true><<<(P * P + 255) / 256, 256, 0, st>>>(d_h1, d_eri, n, P, NS, nw,
-                                                          wimg.as<uint8_t>(), (double)wscale);
+        k_wimg<true><<<(P * P + 255) / 256, 256, 0, st>>>(d_eri, n, P, NS, nw,
+                                                          wimg.as<uint16_t>(), (double)wscale);
     else
-        k_wimg<false><<<(P * P + 255) / 256, 256, 0, st>>>(d_h1, d_eri, n, P, NS, nw,
-                                                           wimg.as<uint8_t>(), (double)wscale);
+        k_wimg<false><<<(P * P + 255) / 256, 256, 0, st>>>(d_eri, n, P, NS, nw,
+                                                           wimg.as<uint16_t>(), (double)wscale);
     KPM_LAUNCHED();
 
     auto build_slots = [&](const SpinTables& T, DevBuf& out) {
@@ -598,7 +657,7 @@ void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
 }
 
 void TcSigma::apply(const float* x, float* y, int ncol, cudaStream_t st) {
-    const uint32_t nc = tmem_cols(P);
+    const uint32_t nc = tmem_cols(P, KR);
     for (int c = 0; c < ncol; ++c) {
         const float* X = x + (size_t)c * dim;
         float* Y = y + (size_t)c * dim;
@@ -610,7 +669,7 @@ void TcSigma::apply(const float* x, float* y, int ncol, cudaStream_t st) {
         // opposite-spin part: rows alpha, columns beta; writes Y
         RowPass p1{X, Y, nsa, nsb, slot_b.as<uint4>(),
                    ta->tgt.as<int32_t>(), ta->pq.as<uint16_t>(), ta->sgn.as<int8_t>(), ta->nexc,
-                   wimg.as<uint4>(), NS, n, nc, am, wscale, gbound, tb->nexc, err.as<int>()};
+                   KR, wimg.as<__half>(), NS, n, nc, am, wscale, gbound, tb->nexc, err.as<int>()};
         int g1 = (int)(nsa < nsm ? nsa : nsm);
         void* args1[] = {&p1};
         KPM_CUDA(cudaLaunchKernel(kernel, dim3(g1), dim3(RP_THREADS), args1, smem_bytes, st));

@@ -8,7 +8,8 @@ namespace kpm {
 // sigma = H x with the two-electron terms contracted on the 5th-generation
 // tensor cores.  See sigma_tc.cu for the formulation.
 struct TcSigma {
-    int n = 0, NS = 0, P = 0;     // orbitals, unordered pairs n(n+1)/2, padded K = N
+    int n = 0, NS = 0, P = 0;     // orbitals, unordered pairs n(n+1)/2, padded N (output slots)
+    int KR = 0;                   // K of the row GEMM: row-string table entries rounded to 16
     int64_t nsa = 0, nsb = 0, dim = 0;
     int nsm = 0;                  // SMs of the device (persistent grid)
     bool fp16 = false;            // operand format: split FP16 (scaled) or split BF16
@@ -18,7 +19,7 @@ struct TcSigma {
     void* kernel = nullptr;       // k_rowpass instantiation for P
     const SpinTables* ta = nullptr;
     const SpinTables* tb = nullptr;
-    DevBuf wimg;                  // W = (pq|rs) over slots as split 16-bit operand image
+    DevBuf wimg;                  // W = (pq|rs) over slot pairs, split into 16-bit pieces
     DevBuf slot_b;                // uint16 [P/8][N_b][8] pair-slot -> target | sign << 15 (N_b: none)
     DenseSS dense;                // same-spin parts (dense GEMMs with F_a, F_b)
     DevBuf err;                   // int error flag (1: a bounded wait ran out)
