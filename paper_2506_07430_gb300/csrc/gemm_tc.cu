@@ -477,6 +477,7 @@ void DenseSS::init(const SpinTables& A, const SpinTables& B, bool same, int* err
     nb = B.ns;
     pa = half_pitch(na);
     pb = half_pitch(nb);
+    xpitch = (nb + 127) / 128 * 128;
     err = err_flag;
     smem = GM_STAGES * STAGE_BYTES + 1024 + 256;
     KPM_CUDA(cudaFuncSetAttribute(k_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -496,14 +497,18 @@ void DenseSS::init(const SpinTables& A, const SpinTables& B, bool same, int* err
     }
 }
 
+void DenseSS::split(const float* x, const float* amax, cudaStream_t st) {
+    xh.ensure((size_t)na * xpitch * 2);
+    xl.ensure((size_t)na * xpitch * 2);
+    k_split_rows<<<2048, 256, 0, st>>>(x, na, nb, nb, xh.as<__half>(), xl.as<__half>(), xpitch,
+                                       amax);
+    KPM_LAUNCHED();
+}
+
 void DenseSS::apply(const float* x, float* y, const float* amax, cudaStream_t st) {
-    // split copies of x: rows (alpha) x cols (beta), and transposed
-    xh.ensure((size_t)na * pb * 2);
-    xl.ensure((size_t)na * pb * 2);
+    // transposed split copy of x (cols beta x rows alpha); the row split is xh/xl
     th.ensure((size_t)nb * pa * 2);
     tl.ensure((size_t)nb * pa * 2);
-    k_split_rows<<<2048, 256, 0, st>>>(x, na, nb, nb, xh.as<__half>(), xl.as<__half>(), pb, amax);
-    KPM_LAUNCHED();
     dim3 tb(32, 8), gt((unsigned)((nb + 31) / 32), (unsigned)((na + 31) / 32));
     k_split_transpose<<<gt, tb, 0, st>>>(x, na, nb, th.as<__half>(), tl.as<__half>(), pa, amax);
     KPM_LAUNCHED();
@@ -511,8 +516,8 @@ void DenseSS::apply(const float* x, float* y, const float* amax, cudaStream_t st
     {
         CUtensorMap a0 = make_map(fb_hi.as<__half>(), nb, nb, pb, GM_BM);
         CUtensorMap a1 = make_map(fb_lo.as<__half>(), nb, nb, pb, GM_BM);
-        CUtensorMap b0 = make_map(xh.as<__half>(), na, nb, pb, GM_BN);
-        CUtensorMap b1 = make_map(xl.as<__half>(), na, nb, pb, GM_BN);
+        CUtensorMap b0 = make_map(xh.as<__half>(), na, nb, xpitch, GM_BN);
+        CUtensorMap b1 = make_map(xl.as<__half>(), na, nb, xpitch, GM_BN);
         GemmArgs g{(int)nb, (int)na, (int)nb, y, nb, 1.0f, amax, (float)wscale_b,
                    nullptr, nullptr, nullptr, err};
         dim3 grid((unsigned)(((nb + GM_BM - 1) / GM_BM) * ((na + GM_BN - 1) / GM_BN)));

@@ -16,6 +16,7 @@ struct DenseSS {
     DevBuf* fa_hi = nullptr;
     DevBuf* fa_lo = nullptr;
     DevBuf* da = nullptr;
+    int64_t xpitch = 0;                       // row pitch of xh/xl: N_b rounded up to 128
     DevBuf xh, xl, th, tl;                    // split copies of x and x^T
     DevBuf fmax;                              // scratch for max |F_off|
     size_t smem = 0;
@@ -24,7 +25,10 @@ struct DenseSS {
     // Builds the split matrices; `same`: alpha and beta strings are identical.
     void init(const SpinTables& A, const SpinTables& B, bool same, int* err_flag,
               cudaStream_t st);
+    // xh/xl = x split into scaled FP16 pieces [N_a][xpitch] (zero padding).
+    void split(const float* x, const float* amax, cudaStream_t st);
     // y += (F_a (x) 1 + 1 (x) F_b) x, the diagonals exactly; amax = device max|x|.
+    // Uses xh/xl from split(x) on the same stream.
     void apply(const float* x, float* y, const float* amax, cudaStream_t st);
 };
 

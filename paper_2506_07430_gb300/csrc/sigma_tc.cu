@@ -66,14 +66,6 @@ __device__ __forceinline__ void tc_fence_before() {
 __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
-__device__ __forceinline__ void tmem_st4(uint32_t taddr, uint32_t a, uint32_t b, uint32_t c,
-                                         uint32_t d) {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};"
-                 ::"r"(taddr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
-}
-__device__ __forceinline__ void tmem_st_wait() {
-    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-}
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
@@ -81,16 +73,22 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
                  : "r"(taddr)
                  : "memory");
 }
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr)
+                 : "memory");
+}
 __device__ __forceinline__ void tmem_ld_wait() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
-// D[tmem] (+)= A[tmem] * B[smem]^T, kind::f16 (BF16 or FP16 operands, FP32 accumulate)
-__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t idesc,
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (BF16 or FP16 operands, FP32 accumulate)
+__device__ __forceinline__ void mma_ss(uint32_t d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                        uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}"
-        ::"r"(d), "r"(a), "l"(bdesc), "r"(idesc), "r"(accumulate) : "memory");
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate) : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t* mbar) {
     asm volatile(
@@ -119,11 +117,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t parity) {
     return ok != 0;
 }
 
-// 4-byte asynchronous global -> shared copy; src_bytes = 0 writes zero
-__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, uint32_t src_bytes) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src),
-                 "r"(src_bytes) : "memory");
-}
 __device__ __forceinline__ void cp_async_commit() {
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -132,9 +125,11 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Shared-memory matrix descriptor, canonical K-major layout without swizzle:
-// 8-row x 16-byte core matrices; LBO = byte distance between core matrices
-// adjacent along K, SBO = between core matrices adjacent along M/N.
+// Shared-memory matrix descriptor, canonical layouts without swizzle: 8 x 16-byte
+// core matrices (128 contiguous bytes); LBO = byte distance between core
+// matrices adjacent along K, SBO = between core matrices adjacent along M/N.
+// K-major: a core matrix row is 8 K-consecutive elements of one M/N index;
+// MN-major: 8 M/N-consecutive elements of one K index.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
@@ -145,26 +140,10 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 }
 
 // Instruction descriptor, kind::f16: D = F32, A/B = BF16 (1) or F16 (0), both
-// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+// K-major (bit 15 set: A MN-major), N >> 3 at bit 17, M >> 4 at bit 24.
 __host__ __device__ constexpr uint32_t instr_desc(int M, int N, bool bf16) {
     return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) |
            ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-template <bool FP16>
-__device__ __forceinline__ uint32_t pack2(float a, float b) {
-    if (FP16) {
-        __half2 h = __floats2half2_rn(a, b);
-        return *reinterpret_cast<uint32_t*>(&h);
-    } else {
-        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-        return *reinterpret_cast<uint32_t*>(&h);
-    }
-}
-template <bool FP16>
-__device__ __forceinline__ float round16(float a) {
-    if (FP16) return __half2float(__float2half_rn(a));
-    return __bfloat162float(__float2bfloat16_rn(a));
 }
 
 __device__ __forceinline__ void slot_pair(int s, int& p, int& q) {
@@ -176,21 +155,21 @@ __device__ __forceinline__ void slot_pair(int s, int& p, int& q) {
 }
 
 struct RowPass {
-    const float* X;
+    const uint16_t* Xh;      // x split into 16-bit pieces (bits of the format), [Nr][xpitch],
+    const uint16_t* Xl;      // scaled by sa(amax); columns [Nc, xpitch) hold zeros
+    int64_t xpitch;          // multiple of 128
     float* Y;
     int64_t Nr, Nc;
     const uint4* tslot8;     // [P/8][Nc]: 8 16-bit entries per chunk of 8 slots (slot 8c+u in
                              // half u of the 128-bit word): target string | sign << 15,
                              // Nc when the slot is absent
-    const int32_t* rtgt;     // [Nr][rnexc] row-string tables
-    const uint16_t* rpq;
-    const int8_t* rsgn;
-    int rnexc;               // table entries per row string (K of the row's GEMM)
-    int KR;                  // rnexc rounded up to 16
-    const __half* wrow;      // W by input slot: NW pieces of [P][P] 16-bit (bits of the format)
-    int NS, n;
+    const int32_t* rtgt;     // [Nr][rnexc] row-string targets
+    const uint16_t* rslot;   // [Nr][rnexc] row-string slot | sign << 15
+    int rnexc;               // table entries per row string
+    int KR;                  // K of the row GEMM: rnexc rounded up to 16
+    const uint16_t* wrow;    // W by input slot: NW pieces of [P][P] 16-bit (bits of the format)
     uint32_t ncols;          // TMEM columns allocated
-    const float* amax;       // device max|X| (operand scaling and fixed-point range)
+    const float* amax;       // device max|x| (operand scaling and fixed-point range)
     float wscale;            // power-of-two scale applied to W in the image
     float gbound;            // max over output slots of sum_k |W[k][s]| (unscaled W)
     int nexc_c;              // table entries per column string (contributions per target)
@@ -200,36 +179,86 @@ struct RowPass {
 constexpr int RP_WARPS = 16;                 // 4 warps per TMEM lane quadrant
 constexpr int RP_THREADS = 32 * RP_WARPS;
 constexpr int RP_MAXK = 96;                  // largest KR: 9 * 10 = 90 entries rounded up
+constexpr uint32_t A_LBO = 2048;             // A stage: K-group (8 entries) stride, bytes
+constexpr uint32_t A_SBO = 128;              // A stage: MN-group (8 columns) stride, bytes
+
+// operand scales, all powers of two (see the kernel comment)
+struct Scales {
+    float sa;      // x -> A
+    float fx;      // value -> fixed point
+    float bscale;  // W image -> B_R, so that D = value * fx
+};
+__device__ __forceinline__ Scales scales(float mx, bool fp16, float wscale, float gbound,
+                                         int nexc_c) {
+    Scales c{1.f, 1.f, 1.f};
+    if (mx > 0.f && isfinite(mx)) {
+        int e;
+        frexpf(mx, &e);  // mx < 2^e
+        if (fp16) c.sa = ldexpf(1.f, 14 - max(e, -90));
+        // every target receives nexc_c terms of magnitude <= max|x| gbound
+        const float bound = 1.02f * (float)nexc_c * mx * gbound;
+        int f = -90;
+        if (bound > 0.f) frexpf(bound, &f);  // bound < 2^f
+        c.fx = ldexpf(1.f, 31 - max(f, -90));
+    }
+    c.bscale = c.fx / (c.sa * wscale);
+    return c;
+}
+
+template <bool FP16>
+__device__ __forceinline__ uint16_t scale16(uint16_t bits, float sc) {
+    if (FP16) {
+        __half h = __float2half_rn(__half2float(__ushort_as_half(bits)) * sc);
+        return __half_as_ushort(h);
+    } else {
+        __nv_bfloat16 h = __float2bfloat16_rn(__bfloat162float(__ushort_as_bfloat16(bits)) * sc);
+        return __bfloat16_as_ushort(h);
+    }
+}
+
+__device__ __forceinline__ void atom_add_shared(uint32_t addr, int v) {
+    asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
 
 // P: padded N (multiple of 16); FP16: operand format (else BF16); NW: pieces of W.
-// Per row R the K dimension holds R's own table entries e (KR = rnexc rounded up
-// to 16): A[J][e] = X[tgt_e, J], and the row's B, B_R[s][e] = sgn_e W[slot(e)][s],
-// is gathered from the W image into shared memory (canonical K-major layout
-// without swizzle).  MMA passes: A_hi B_j for every piece j, plus A_lo B_0.
 //
-// Work split: the KR entries form KR/8 chunks of 8 (A build) and the P output
-// slots P/8 chunks (scatter); the 4 warps of a lane quadrant take chunks
-// round-robin.  Per tile t the CTA waits for MMA(t), copies D(t) into
-// registers, issues MMA(t+1), builds A(t+2) into the buffer MMA(t) has finished
-// with, starts the asynchronous gather copies of tile t+3 into shared memory
-// and scatters D(t).  The gather of a tile is thus in flight for a whole
-// iteration, and the scatter's table words, loaded at the start of the
-// iteration, arrive during the build.
+// Row R's GEMM: D[J][s] = sum_e A[J][e] B_R[s][e], K = the row's table entries
+// e (KR = rnexc rounded up to 16), A[J][e] = x[tgt_e][J] (x pre-split into
+// 16-bit hi/lo pieces), B_R[s][e] = sgn_e W[slot(e)][s] bscale.  bscale folds
+// the operand scales and the fixed-point factor into B, so D is already the
+// fixed-point value and the scatter only rounds it to an integer.
+//
+// A is staged in shared memory in the canonical MN-major layout without
+// swizzle (8 columns x 8 entries per 128-byte core matrix; MN-group stride
+// A_SBO, K-group stride A_LBO) by 16-byte cp.async copies straight from the
+// split rows of x, two stages deep; B_R is gathered once per row (canonical
+// K-major layout without swizzle).  MMA passes: A_hi B_j for every piece j,
+// plus A_lo B_0; D accumulates in tensor memory.
+//
+// Per tile t: wait for MMA(t), copy D(t) to registers, start the copies of
+// tile t+2 into the stage MMA(t) has finished with, wait for the copies of
+// tile t+1, issue MMA(t+1), and scatter D(t) with 32-bit fixed-point shared
+// atomics.  The 4 warps of a TMEM lane quadrant share the P output slots
+// evenly (chunks of 8 round-robin, a remainder of two chunks in halves).
 template <int P, bool FP16, int NW>
 __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
     constexpr int NCH = P / 8;                     // output chunks of 8 slots
-    constexpr int MAXC = (NCH + 3) / 4;            // output chunks per warp (upper bound)
-    constexpr int MAXA = (RP_MAXK / 8 + 3) / 4;    // input chunks per warp (upper bound)
+    constexpr int NFULL = NCH / 4;                 // full chunks per warp
+    constexpr bool HALF = (NCH % 4) == 2;          // two chunks left: one half-chunk per warp
+    static_assert(NCH % 4 == 0 || NCH % 4 == 2, "P is a multiple of 16");
+    constexpr int MAXQ = RP_MAXK / 16;             // 16-byte copies per thread per tile (upper bound)
     extern __shared__ __align__(1024) unsigned char smem[];
     const int KR = p.KR;
     const int64_t Nc = p.Nc;
-    uint8_t* sB = smem;                                               // NW pieces of P x KR
-    const uint32_t piece_bytes = (uint32_t)(P * KR * 2);
-    int* srow = reinterpret_cast<int*>(smem + NW * piece_bytes);      // Nc + 1, fixed point
-    int32_t* rje = srow + (Nc + 1);                                   // [RP_MAXK] source rows
-    float* sX = reinterpret_cast<float*>(
-        (reinterpret_cast<uintptr_t>(rje + RP_MAXK) + 15) & ~uintptr_t(15));  // [2][KR][128]
-    uintptr_t tail = reinterpret_cast<uintptr_t>(sX + 2 * KR * 128);
+    const uint32_t a_piece = (uint32_t)KR * 256u;                     // one piece of one stage
+    uint8_t* sA = smem;                                               // [2 stages][2 pieces]
+    uint8_t* sB = smem + 4 * a_piece;                                 // NW pieces of P x KR
+    const uint32_t b_piece = (uint32_t)(P * KR * 2);
+    int* srow = reinterpret_cast<int*>(sB + NW * b_piece);            // Nc + 1, fixed point
+    int64_t* rowoff = reinterpret_cast<int64_t*>(
+        (reinterpret_cast<uintptr_t>(srow + Nc + 1) + 15) & ~uintptr_t(15));  // [RP_MAXK]
+    uint16_t* rsl = reinterpret_cast<uint16_t*>(rowoff + RP_MAXK);    // [RP_MAXK]
+    uintptr_t tail = (reinterpret_cast<uintptr_t>(rsl + RP_MAXK) + 15) & ~uintptr_t(15);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(tail);
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(mbar + 1);
     int* abort_flag = reinterpret_cast<int*>(tmem_holder + 1);
@@ -253,132 +282,101 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
     tc_fence_after();
     const uint32_t tbase = *tmem_holder;
     const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
-    constexpr uint32_t idesc = instr_desc(128, P, !FP16);
-    const uint32_t sB_addr = smem_u32(sB);
-    const uint32_t sX_addr = smem_u32(sX);
-    const uint32_t SBO = 16u * (uint32_t)KR, LBO = 128u;
+    constexpr uint32_t idesc = instr_desc(128, P, !FP16) | (1u << 15);  // A MN-major
+    const uint32_t sA_addr = smem_u32(sA), sB_addr = smem_u32(sB);
+    const uint32_t srow_addr = smem_u32(srow);
+    const uint32_t SBO_B = 16u * (uint32_t)KR;
     const int ntiles = (int)((Nc + 127) / 128);
-    const int nchA = KR / 8;
-    float sa = 1.f, fx = 1.f;
-    {
-        const float mx = *p.amax;
-        if (mx > 0.f && isfinite(mx)) {
-            int e;
-            frexpf(mx, &e);  // mx < 2^e; A entries are single values of x
-            if (FP16) sa = ldexpf(1.f, 14 - max(e, -90));
-            // every target receives nexc_c terms of magnitude <= max|x| gbound
-            const float bound = 1.02f * (float)p.nexc_c * mx * p.gbound;
-            int f = -90;
-            if (bound > 0.f) frexpf(bound, &f);  // bound < 2^f
-            fx = ldexpf(1.f, 31 - max(f, -90));
-        }
-    }
-    const float unscale = fx / (sa * p.wscale);   // D -> fixed point
-    const float inv_fx = 1.f / fx;
+    const int nq = KR / 16;                 // copies per thread per tile
+    const Scales sc = scales(*p.amax, FP16, p.wscale, p.gbound, p.nexc_c);
+    const float inv_fx = 1.f / sc.fx;
     const uint32_t absent = (uint32_t)Nc;
     uint32_t phase = 0;
 
-    // stage the gather X[tgt_e, J] of tile t for this thread's entry chunks
-    // (4-byte cp.async: rows of X are not 16-byte aligned in general)
+    // this thread's 16-byte copies: piece/K-group u = (tid >> 7) + 4 i, entry
+    // (u mod KR/8) * 8 + (tid & 7), column group (tid >> 3) & 15
+    const int eo = tid & 7, grp = (tid >> 3) & 15;
+    int64_t srcoff[MAXQ];
+    uint32_t dstoff[MAXQ];
+
     auto copies = [&](int t) {
-        const int64_t jc = (int64_t)t * 128 + m;
-        const bool valid = jc < Nc;
-        const uint32_t dst0 = sX_addr + (uint32_t)((t & 1) * KR) * 512u + (uint32_t)m * 4u;
+        const int64_t j0 = (int64_t)t * 128;
+        const uint32_t st = sA_addr + (uint32_t)(t & 1) * 2u * a_piece;
 #pragma unroll
-        for (int k = 0; k < MAXA; ++k) {
-            const int c = wq + 4 * k;
-            if (c < nchA) {
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int e = c * 8 + u;
-                    const int r = rje[e];
-                    const bool ok = valid && r >= 0;
-                    const float* src = ok ? p.X + (int64_t)r * Nc + jc : p.X;
-                    cp_async4(dst0 + (uint32_t)e * 512u, src, ok ? 4u : 0u);
-                }
+        for (int i = 0; i < MAXQ; ++i) {
+            if (i < nq) {
+                const int u = (tid >> 7) + 4 * i;
+                const uint16_t* base = u < KR / 8 ? p.Xh : p.Xl;
+                const bool ok = srcoff[i] >= 0;
+                const uint16_t* src = ok ? base + srcoff[i] + j0 : base;
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(st + dstoff[i]),
+                             "l"(src), "r"(ok ? 16u : 0u) : "memory");
             }
         }
         cp_async_commit();
     };
 
-    // A(t) = split X gather of tile t (staged by copies(t)) -> TMEM buffer buf
-    auto build = [&](int t, int buf) {
-        const float* xs = sX + (size_t)((t & 1) * KR) * 128 + m;
-        const uint32_t a_hi = tbase + lane_base + (uint32_t)(buf * KR);
-        const uint32_t a_lo = a_hi + (uint32_t)(KR / 2);
-#pragma unroll
-        for (int k = 0; k < MAXA; ++k) {
-            const int c = wq + 4 * k;
-            if (c < nchA) {
-                uint32_t hi[4], lo[4];
-#pragma unroll
-                for (int u = 0; u < 8; u += 2) {
-                    const float v0 = xs[(c * 8 + u) * 128] * sa;
-                    const float v1 = xs[(c * 8 + u + 1) * 128] * sa;
-                    const float h0 = round16<FP16>(v0), h1 = round16<FP16>(v1);
-                    hi[u / 2] = pack2<FP16>(h0, h1);
-                    lo[u / 2] = pack2<FP16>(v0 - h0, v1 - h1);
-                }
-                const uint32_t col = (uint32_t)(c * 4);
-                tmem_st4(a_hi + col, hi[0], hi[1], hi[2], hi[3]);
-                tmem_st4(a_lo + col, lo[0], lo[1], lo[2], lo[3]);
-            }
-        }
-    };
-
     auto issue = [&](int t) {
-        const int buf = t & 1;
-        const uint32_t a_hi = tbase + (uint32_t)(buf * KR);
-        const uint32_t a_lo = a_hi + (uint32_t)(KR / 2);
-        const uint32_t d = tbase + (uint32_t)(2 * KR);
+        const uint32_t st = sA_addr + (uint32_t)(t & 1) * 2u * a_piece;
+        const uint32_t d = tbase;
         const int ksteps = KR / 16;
 #pragma unroll
         for (int pass = 0; pass < NW + 1; ++pass) {
-            // pass 0: A_hi W_0, pass 1: A_lo W_0, pass j+1 (j >= 1): A_hi W_j
-            const uint32_t a = (pass == 1) ? a_lo : a_hi;
+            // pass 0: A_hi B_0, pass 1: A_lo B_0, pass j+1 (j >= 1): A_hi B_j
+            const uint32_t a = st + (pass == 1 ? a_piece : 0u);
             const int piece = pass <= 1 ? 0 : pass - 1;
-            const uint32_t bbase = sB_addr + (uint32_t)piece * piece_bytes;
+            const uint32_t bb = sB_addr + (uint32_t)piece * b_piece;
             for (int j = 0; j < ksteps; ++j) {
-                uint64_t bd = smem_desc(bbase + (uint32_t)(j * 256), LBO, SBO);
-                mma_ts(d, a + (uint32_t)(j * 8), bd, idesc, (pass | j) != 0);
+                const uint64_t ad = smem_desc(a + (uint32_t)j * 2u * A_LBO, A_LBO, A_SBO);
+                const uint64_t bd = smem_desc(bb + (uint32_t)(j * 256), 128u, SBO_B);
+                mma_ss(d, ad, bd, idesc, (pass | j) != 0);
             }
         }
         mma_commit(mbar);
     };
 
-    auto load_d = [&](uint32_t (&dr)[MAXC][8]) {
-        const uint32_t dcol = tbase + lane_base + (uint32_t)(2 * KR);
+    constexpr int NLD = NFULL + (HALF ? 1 : 0);
+    auto load_d = [&](uint32_t (&dr)[NLD][8]) {
+        const uint32_t dcol = tbase + lane_base;
 #pragma unroll
-        for (int k = 0; k < MAXC; ++k) {
-            const int c = wq + 4 * k;
-            if (c < NCH) tmem_ld8(dcol + (uint32_t)(c * 8), dr[k]);
+        for (int k = 0; k < NFULL; ++k) tmem_ld8(dcol + (uint32_t)((wq + 4 * k) * 8), dr[k]);
+        if (HALF) {
+            const uint32_t c = (uint32_t)((NFULL * 4 + (wq >> 1)) * 8 + (wq & 1) * 4);
+            tmem_ld4(dcol + c, dr[NLD - 1]);
         }
         tmem_ld_wait();
     };
 
-    auto load_words = [&](int t, uint4 (&w4)[MAXC]) {
+    auto load_words = [&](int t, uint32_t (&w)[NLD][4]) {
         const int64_t jc = (int64_t)t * 128 + m;
         const int64_t jcc = jc < Nc ? jc : Nc - 1;
 #pragma unroll
-        for (int k = 0; k < MAXC; ++k) {
-            const int c = wq + 4 * k;
-            if (c < NCH) w4[k] = __ldg(p.tslot8 + (int64_t)c * Nc + jcc);
+        for (int k = 0; k < NFULL; ++k) {
+            const uint4 v = __ldg(p.tslot8 + (int64_t)(wq + 4 * k) * Nc + jcc);
+            w[k][0] = v.x; w[k][1] = v.y; w[k][2] = v.z; w[k][3] = v.w;
+        }
+        if (HALF) {
+            const uint2* q = reinterpret_cast<const uint2*>(
+                p.tslot8 + (int64_t)(NFULL * 4 + (wq >> 1)) * Nc + jcc);
+            const uint2 v = __ldg(q + (wq & 1));
+            w[NLD - 1][0] = v.x; w[NLD - 1][1] = v.y;
         }
     };
 
-    auto scatter = [&](int t, const uint32_t (&dr)[MAXC][8], const uint4 (&w4)[MAXC]) {
+    auto scatter = [&](int t, const uint32_t (&dr)[NLD][8], const uint32_t (&w)[NLD][4]) {
         const bool valid = (int64_t)t * 128 + m < Nc;
 #pragma unroll
-        for (int k = 0; k < MAXC; ++k) {
-            const int c = wq + 4 * k;
-            if (c < NCH) {
-                const uint32_t w[4] = {w4[k].x, w4[k].y, w4[k].z, w4[k].w};
+        for (int k = 0; k < NLD; ++k) {
+            const int nu = (HALF && k == NLD - 1) ? 4 : 8;
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const uint32_t e = (w[u >> 1] >> (16 * (u & 1))) & 0xFFFFu;
-                    const uint32_t tg = e & 0x7FFFu;
-                    const int q = __float2int_rn(__uint_as_float(dr[k][u]) * unscale);
-                    if (valid && tg != absent) atomicAdd(srow + tg, (e & 0x8000u) ? -q : q);
+            for (int u = 0; u < 8; ++u) {
+                if (u < nu) {
+                    const uint32_t ww = w[k][u >> 1];
+                    // entry u: tgt | sign << 15 in half u & 1 of word u >> 1
+                    const uint32_t tg = (u & 1) ? (ww >> 16) & 0x7FFFu : ww & 0x7FFFu;
+                    const uint32_t sg = (u & 1) ? (ww & 0x80000000u) : (ww << 16) & 0x80000000u;
+                    const int q = __float2int_rn(__uint_as_float(dr[k][u] ^ sg));
+                    if (valid && tg != absent) atom_add_shared(srow_addr + tg * 4u, q);
                 }
             }
         }
@@ -399,75 +397,75 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
     };
 
     for (int64_t ir = blockIdx.x; ir < p.Nr; ir += gridDim.x) {
-        // row set-up: zero sigma, the row's source rows, and its B (signs folded in)
+        // row set-up: zero sigma; the row's source rows, slots and signs
         for (int64_t j = tid; j <= Nc; j += RP_THREADS) srow[j] = 0;
-        for (int e = tid; e < RP_MAXK; e += RP_THREADS)
-            rje[e] = e < p.rnexc ? p.rtgt[ir * p.rnexc + e] : -1;
-        {
-            const uint16_t* wsrc = reinterpret_cast<const uint16_t*>(p.wrow);
-            const int tot = NW * P * KR;
-            for (int i = tid; i < tot; i += RP_THREADS) {
-                const int piece = i / (P * KR);
-                const int rem = i % (P * KR);
-                const int e = rem / P, nn = rem % P;   // consecutive threads: consecutive nn
+        for (int e = tid; e < RP_MAXK; e += RP_THREADS) {
+            const bool in = e < p.rnexc;
+            rowoff[e] = in ? (int64_t)p.rtgt[ir * p.rnexc + e] * p.xpitch : -1;
+            rsl[e] = in ? p.rslot[ir * p.rnexc + e] : (uint16_t)0xFFFFu;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < MAXQ; ++i) {
+            if (i < nq) {
+                const int u = (tid >> 7) + 4 * i;
+                const int kc = u % (KR / 8), piece = u / (KR / 8);
+                const int64_t ro = rowoff[kc * 8 + eo];
+                srcoff[i] = ro >= 0 ? ro + 8 * grp : -1;
+                dstoff[i] = (uint32_t)piece * a_piece + (uint32_t)grp * A_SBO +
+                            (uint32_t)kc * A_LBO + (uint32_t)eo * 16u;
+            }
+        }
+        // B_R[s][e] = sgn_e W_piece[slot(e)][s] bscale (canonical K-major layout)
+#pragma unroll 1
+        for (int piece = 0; piece < NW; ++piece) {
+            const uint16_t* wsrc = p.wrow + (size_t)piece * P * P;
+            uint8_t* dst = sB + piece * b_piece;
+            for (int i = tid; i < KR * P; i += RP_THREADS) {
+                const int e = i / P, nn = i - (i / P) * P;
+                const uint16_t r = rsl[e];
                 uint16_t v = 0;
-                if (e < p.rnexc) {
-                    const int g = p.rpq[ir * p.rnexc + e];
-                    int a = g / p.n, b = g % p.n;
-                    if (a > b) { int t = a; a = b; b = t; }
-                    const int sl = b * (b + 1) / 2 + a;
-                    v = wsrc[((size_t)piece * P + sl) * P + nn];
-                    if (p.rsgn[ir * p.rnexc + e] < 0) v ^= 0x8000u;   // exact negation
+                if (r != 0xFFFFu) {
+                    v = scale16<FP16>(__ldg(wsrc + (size_t)(r & 0x7FFFu) * P + nn), sc.bscale);
+                    v ^= (uint16_t)(r & 0x8000u);   // exact negation
                 }
-                const uint32_t off = (uint32_t)piece * piece_bytes + (uint32_t)(nn / 8) * SBO +
-                                     (uint32_t)(e / 8) * 128 + (uint32_t)(nn % 8) * 16 +
-                                     (uint32_t)(e % 8) * 2;
-                *reinterpret_cast<uint16_t*>(sB + off) = v;
+                const uint32_t off = (uint32_t)(nn >> 3) * SBO_B + (uint32_t)(e >> 3) * 128u +
+                                     (uint32_t)(nn & 7) * 16u + (uint32_t)(e & 7) * 2u;
+                *reinterpret_cast<uint16_t*>(dst + off) = v;
             }
         }
         fence_proxy_async_smem();
-        __syncthreads();
 
-        // tiles: copies(t + 3) and build(t + 2) run while MMA(t + 1) does;
-        // stage t & 1 holds tile t's gather from copies(t) until build(t)
+        // tiles (stage t & 1 holds tile t's A from copies(t) until MMA(t) is done)
         copies(0);
-        if (ntiles > 1) copies(1);
-        if (ntiles > 1) cp_async_wait<1>(); else cp_async_wait<0>();
-        build(0, 0);
-        tmem_st_wait();
+        if (ntiles > 1) copies(1); else cp_async_commit();
+        cp_async_wait<1>();
+        fence_proxy_async_smem();
         tc_fence_before();
         __syncthreads();
         if (tid == 0) {
             tc_fence_after();
             issue(0);
         }
-        if (ntiles > 1) {
-            cp_async_wait<0>();
-            build(1, 1);
-        }
-        if (ntiles > 2) copies(2);
         for (int t = 0; t < ntiles; ++t) {
-            uint4 w4[MAXC];
-            load_words(t, w4);
+            uint32_t w[NLD][4];
+            load_words(t, w);
             wait_mma();
             __syncthreads();
             if (*abort_flag) break;
             tc_fence_after();
-            uint32_t dr[MAXC][8];
+            uint32_t dr[NLD][8];
             load_d(dr);
-            tmem_st_wait();
+            if (t + 2 < ntiles) copies(t + 2); else cp_async_commit();
+            cp_async_wait<1>();
+            fence_proxy_async_smem();
             tc_fence_before();
             __syncthreads();
             if (t + 1 < ntiles && tid == 0) {
                 tc_fence_after();
                 issue(t + 1);
             }
-            if (t + 2 < ntiles) {
-                cp_async_wait<0>();
-                build(t + 2, t & 1);
-            }
-            if (t + 3 < ntiles) copies(t + 3);
-            scatter(t, dr, w4);
+            scatter(t, dr, w);
         }
         cp_async_wait<0>();
         __syncthreads();
@@ -550,15 +548,40 @@ __global__ void k_slot_table(const int32_t* __restrict__ tgt, const uint16_t* __
         (uint16_t)(tgt[i] | (sgn[i] < 0 ? 0x8000 : 0));
 }
 
-uint32_t tmem_cols(int P, int KR) {
-    uint32_t need = (uint32_t)(2 * KR + P), c = 32;
+// row-string slot table: entry e of string r -> slot({p,q}) | (sgn < 0) << 15
+__global__ void k_row_slots(const uint16_t* __restrict__ pq, const int8_t* __restrict__ sgn,
+                            int64_t count, int n, uint16_t* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    int a = pq[i] / n, b = pq[i] % n;
+    if (a > b) { int t = a; a = b; b = t; }
+    out[i] = (uint16_t)((b * (b + 1) / 2 + a) | (sgn[i] < 0 ? 0x8000 : 0));
+}
+
+// x [R][Cn] -> hi/lo BF16 pieces [R][pitch] (BF16 needs no scale); zero padding
+__global__ void k_split_rows_bf16(const float* __restrict__ src, int64_t R, int64_t Cn,
+                                  uint16_t* __restrict__ hi, uint16_t* __restrict__ lo,
+                                  int64_t pitch) {
+    const int64_t total = R * pitch;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / pitch, c = i % pitch;
+        const float v = c < Cn ? src[r * Cn + c] : 0.f;
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        hi[i] = __bfloat16_as_ushort(h);
+        lo[i] = __bfloat16_as_ushort(__float2bfloat16_rn(v - __bfloat162float(h)));
+    }
+}
+
+uint32_t tmem_cols(int P) {
+    uint32_t need = (uint32_t)P, c = 32;
     while (c < need) c <<= 1;
     return c;
 }
 
 size_t rowpass_smem(int P, int NW, int KR, int64_t Nc) {
-    return (size_t)2 * NW * P * KR + 4 * (size_t)(Nc + 1) + 4 * RP_MAXK + 16 +
-           (size_t)2 * KR * 128 * 4 + 64;
+    return (size_t)4 * KR * 256 + (size_t)2 * NW * P * KR + 4 * (size_t)(Nc + 1) + 16 +
+           10 * RP_MAXK + 16 + 64;
 }
 
 template <int P>
@@ -598,7 +621,7 @@ void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
     nw = fp16 ? 3 : 2;
     kernel = rowpass_kernel(P, fp16);
     KR = ((A.nexc + 15) / 16) * 16;
-    if (!kernel || KR > RP_MAXK || tmem_cols(P, KR) > 512 || A.ns > 32766 || B.ns > 32766)
+    if (!kernel || KR > RP_MAXK || A.ns > 32766 || B.ns > 32766)
         KPM_THROW(KPM_EUNSUPPORTED, "tensor-core sigma supports up to 16 orbitals");
     int dev = 0;
     KPM_CUDA(cudaGetDevice(&dev));
@@ -650,6 +673,15 @@ void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
         }
     };
     build_slots(B, slot_b);
+    {
+        const int64_t ne = A.ns * (int64_t)A.nexc;
+        rslot_a.alloc((size_t)(ne > 0 ? ne : 1) * sizeof(uint16_t));
+        if (ne > 0) {
+            k_row_slots<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
+                A.pq.as<uint16_t>(), A.sgn.as<int8_t>(), ne, n, rslot_a.as<uint16_t>());
+            KPM_LAUNCHED();
+        }
+    }
     err.alloc(sizeof(int));
     amax.alloc(2 * sizeof(unsigned));
     KPM_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
@@ -657,7 +689,8 @@ void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
 }
 
 void TcSigma::apply(const float* x, float* y, int ncol, cudaStream_t st) {
-    const uint32_t nc = tmem_cols(P, KR);
+    const uint32_t nc = tmem_cols(P);
+    const int64_t xp = dense.xpitch;
     for (int c = 0; c < ncol; ++c) {
         const float* X = x + (size_t)c * dim;
         float* Y = y + (size_t)c * dim;
@@ -666,10 +699,23 @@ void TcSigma::apply(const float* x, float* y, int ncol, cudaStream_t st) {
         k_absmax<<<1024, 256, 0, st>>>(X, dim, amax.as<unsigned>());
         KPM_LAUNCHED();
         const float* am = reinterpret_cast<const float*>(amax.p);
+        // split x: the FP16 pieces serve the row pass and the beta GEMM
+        dense.split(X, am, st);
+        const uint16_t* xh = dense.xh.as<uint16_t>();
+        const uint16_t* xl = dense.xl.as<uint16_t>();
+        if (!fp16) {
+            xbh.ensure((size_t)nsa * xp * 2);
+            xbl.ensure((size_t)nsa * xp * 2);
+            k_split_rows_bf16<<<2048, 256, 0, st>>>(X, nsa, nsb, xbh.as<uint16_t>(),
+                                                    xbl.as<uint16_t>(), xp);
+            KPM_LAUNCHED();
+            xh = xbh.as<uint16_t>();
+            xl = xbl.as<uint16_t>();
+        }
         // opposite-spin part: rows alpha, columns beta; writes Y
-        RowPass p1{X, Y, nsa, nsb, slot_b.as<uint4>(),
-                   ta->tgt.as<int32_t>(), ta->pq.as<uint16_t>(), ta->sgn.as<int8_t>(), ta->nexc,
-                   KR, wimg.as<__half>(), NS, n, nc, am, wscale, gbound, tb->nexc, err.as<int>()};
+        RowPass p1{xh, xl, xp, Y, nsa, nsb, slot_b.as<uint4>(),
+                   ta->tgt.as<int32_t>(), rslot_a.as<uint16_t>(), ta->nexc, KR,
+                   wimg.as<uint16_t>(), nc, am, wscale, gbound, tb->nexc, err.as<int>()};
         int g1 = (int)(nsa < nsm ? nsa : nsm);
         void* args1[] = {&p1};
         KPM_CUDA(cudaLaunchKernel(kernel, dim3(g1), dim3(RP_THREADS), args1, smem_bytes, st));

@@ -20,6 +20,8 @@ struct TcSigma {
     const SpinTables* ta = nullptr;
     const SpinTables* tb = nullptr;
     DevBuf wimg;                  // W = (pq|rs) over slot pairs, split into 16-bit pieces
+    DevBuf rslot_a;               // uint16 [N_a][nexc_a] entry -> slot | sign << 15
+    DevBuf xbh, xbl;              // BF16 pieces of x (KPM_MIXED_BF16; FP16 pieces live in dense)
     DevBuf slot_b;                // uint16 [P/8][N_b][8] pair-slot -> target | sign << 15 (N_b: none)
     DenseSS dense;                // same-spin parts (dense GEMMs with F_a, F_b)
     DevBuf err;                   // int error flag (1: a bounded wait ran out)
