@@ -16,22 +16,16 @@
 // (<I|E_pq|J> = <J|E_qp|I> turns the outer excitation into a scatter from J.)
 //
 // GEMM per tile: M = 128 columns J, K = KR (the row's nexc entries rounded up
-// to 16), N = P (NS + 1 rounded up to 16).  A is written by the CUDA cores
-// straight into tensor memory (tcgen05.st, one TMEM lane per column J); B_R is
-// gathered once per row from the W image into shared memory (canonical K-major
-// layout without swizzle, signs folded in); D accumulates in tensor memory in
-// FP32.  Operands are split into 16-bit pieces (FP16 with power-of-two scales:
-// x in 2, W in 3 pieces, 4 MMAs; or BF16 2 + 2, 3 MMAs).  The epilogue reads D
+// to 16), N = P (NS + 1 rounded up to 16), operands in shared memory, D in
+// tensor memory (FP32).  Operands are split into two 16-bit pieces each (FP16
+// with power-of-two scales, or BF16), and three MMAs keep every product term
+// above 2^-22 relative: A_hi B_0, A_hi B_1, A_lo B_0.  The epilogue reads D
 // (tcgen05.ld) and scatters into the row's sigma in shared memory with 32-bit
 // fixed-point integer atomics (order-independent, so the result is
-// reproducible bit for bit).
-//
-// One CTA (16 warps) per SM, persistent over rows; the 4 warps of each TMEM lane
-// quadrant take chunks of 8 (entries or slots) round-robin.  Per tile t the CTA waits for MMA(t),
-// copies D(t) to registers, issues MMA(t+1), builds A(t+2) and scatters D(t),
-// so the tensor core runs while the CUDA cores build and scatter.  Waits on the
-// MMA-completion mbarrier are bounded (about two seconds); on expiry the kernel
-// records an error, frees its TMEM and returns.
+// reproducible bit for bit).  One CTA per SM, persistent over rows; the kernel
+// comment of k_rowpass gives the pipeline.  Every wait on an mbarrier is
+// bounded (about two seconds); on expiry the kernel records an error, frees
+// its tensor memory and returns.
 #include "sigma_tc.cuh"
 
 #include <cuda_bf16.h>
@@ -105,18 +99,6 @@ __device__ __forceinline__ void fence_mbar_init() {
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(mbar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
 __device__ __forceinline__ void cp_async_commit() {
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -173,10 +155,15 @@ struct RowPass {
     float wscale;            // power-of-two scale applied to W in the image
     float gbound;            // max over output slots of sum_k |W[k][s]| (unscaled W)
     int nexc_c;              // table entries per column string (contributions per target)
+    int NS;                  // slots in use (n(n+1)/2); slots [NS, P) are padding
+    int nst;                 // A stages in shared memory (2 or 3)
     int* err;
 };
 
-constexpr int RP_WARPS = 16;                 // 4 warps per TMEM lane quadrant
+constexpr int RP_SCATTER_WARPS = 16;         // 4 per TMEM lane quadrant
+constexpr int RP_COPY_WARPS = 3;             // cp.async producers (warps 16-18)
+constexpr int RP_MMA_WARP = RP_SCATTER_WARPS + RP_COPY_WARPS;   // MMA issue (one thread)
+constexpr int RP_WARPS = RP_SCATTER_WARPS + RP_COPY_WARPS + 1;
 constexpr int RP_THREADS = 32 * RP_WARPS;
 constexpr int RP_MAXK = 96;                  // largest KR: 9 * 10 = 90 entries rounded up
 constexpr uint32_t A_LBO = 2048;             // A stage: K-group (8 entries) stride, bytes
@@ -216,8 +203,45 @@ __device__ __forceinline__ uint16_t scale16(uint16_t bits, float sc) {
     }
 }
 
-__device__ __forceinline__ void atom_add_shared(uint32_t addr, int v) {
-    asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, uint32_t& r0, uint32_t& r1) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
+                 : "=r"(r0), "=r"(r1)
+                 : "r"(taddr)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+
+// try_wait that may suspend the thread for up to ~hint_ns until the phase completes
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* mbar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(mbar)), "r"(parity), "r"(100000u)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase (the waiting thread is suspended, not
+// spinning); false (and the CTA's abort flag set) when the wait ran out or
+// another role has aborted.
+__device__ __forceinline__ bool wait_phase(uint64_t* mbar, uint32_t parity, volatile int* abort_flag,
+                                           int* err) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait_sleep(mbar, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > WAIT_CYCLES) {
+            *abort_flag = 1;
+            atomicExch(err, 1);
+            return false;
+        }
+    }
+    return true;
 }
 
 // P: padded N (multiple of 16); FP16: operand format (else BF16); NW: pieces of W.
@@ -231,45 +255,60 @@ __device__ __forceinline__ void atom_add_shared(uint32_t addr, int v) {
 // A is staged in shared memory in the canonical MN-major layout without
 // swizzle (8 columns x 8 entries per 128-byte core matrix; MN-group stride
 // A_SBO, K-group stride A_LBO) by 16-byte cp.async copies straight from the
-// split rows of x, two stages deep; B_R is gathered once per row (canonical
-// K-major layout without swizzle).  MMA passes: A_hi B_j for every piece j,
-// plus A_lo B_0; D accumulates in tensor memory.
+// split rows of x, nst (3, else 2) stages deep; B_R is gathered once per row
+// (canonical K-major layout without swizzle).  MMA passes: A_hi B_j for every
+// piece j of W, plus A_lo B_0; D accumulates in tensor memory, two buffers deep.
 //
-// Per tile t: wait for MMA(t), copy D(t) to registers, start the copies of
-// tile t+2 into the stage MMA(t) has finished with, wait for the copies of
-// tile t+1, issue MMA(t+1), and scatter D(t) with 32-bit fixed-point shared
-// atomics.  The 4 warps of a TMEM lane quadrant share the P output slots
-// evenly (chunks of 8 round-robin, a remainder of two chunks in halves).
+// Warp roles, synchronised per tile by mbarriers only (waiting threads are
+// suspended on the barrier, so they take no issue slots from the others):
+//   copy (warps 16-18, a third of the copies each): copies of tile t into
+//     stage t % nst once MMA(t - nst) has released it; once they have landed
+//     (and been fenced for the async proxy), each arrives on "A full";
+//   MMA (warp 19, one thread): MMA(t) once A(t) is full and the scatter warps
+//     have released D buffer t & 1; tcgen05.commit then signals "stage free"
+//     and "D full";
+//   scatter (warps 0-15, 4 per TMEM lane quadrant, one column J per thread):
+//     wait for D(t), copy it to registers, release the D buffer, and add every
+//     present slot into the row's sigma in shared memory with 32-bit
+//     fixed-point atomics (order-independent: bitwise reproducible).  The 4
+//     warps of a quadrant share the NS used slots evenly (chunks of 8
+//     round-robin, the remaining chunks split in pairs of slots).
+// Rows are separated by CTA barriers (set-up of the next row's B_R and sigma).
 template <int P, bool FP16, int NW>
 __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
-    constexpr int NCH = P / 8;                     // output chunks of 8 slots
-    constexpr int NFULL = NCH / 4;                 // full chunks per warp
-    constexpr bool HALF = (NCH % 4) == 2;          // two chunks left: one half-chunk per warp
-    static_assert(NCH % 4 == 0 || NCH % 4 == 2, "P is a multiple of 16");
-    constexpr int MAXQ = RP_MAXK / 16;             // 16-byte copies per thread per tile (upper bound)
+    constexpr int MAXF = P >= 32 ? P / 32 : 1;     // full chunks per scatter warp (upper bound)
     extern __shared__ __align__(1024) unsigned char smem[];
     const int KR = p.KR;
     const int64_t Nc = p.Nc;
     const uint32_t a_piece = (uint32_t)KR * 256u;                     // one piece of one stage
-    uint8_t* sA = smem;                                               // [2 stages][2 pieces]
-    uint8_t* sB = smem + 4 * a_piece;                                 // NW pieces of P x KR
+    const uint32_t nst = (uint32_t)p.nst;
+    uint8_t* sA = smem;                                               // [nst stages][2 pieces]
+    uint8_t* sB = smem + 2 * nst * a_piece;                           // NW pieces of P x KR
     const uint32_t b_piece = (uint32_t)(P * KR * 2);
     int* srow = reinterpret_cast<int*>(sB + NW * b_piece);            // Nc + 1, fixed point
     int64_t* rowoff = reinterpret_cast<int64_t*>(
         (reinterpret_cast<uintptr_t>(srow + Nc + 1) + 15) & ~uintptr_t(15));  // [RP_MAXK]
     uint16_t* rsl = reinterpret_cast<uint16_t*>(rowoff + RP_MAXK);    // [RP_MAXK]
     uintptr_t tail = (reinterpret_cast<uintptr_t>(rsl + RP_MAXK) + 15) & ~uintptr_t(15);
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(tail);
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(mbar + 1);
-    int* abort_flag = reinterpret_cast<int*>(tmem_holder + 1);
+    uint64_t* afree = reinterpret_cast<uint64_t*>(tail);   // [3] stage s free (MMA done)
+    uint64_t* afull = afree + 3;                           // [3] stage s copied
+    uint64_t* dfull = afree + 6;                           // [2] D buffer d written
+    uint64_t* dfree = afree + 8;                           // [2] D buffer d read (16 warps)
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(afree + 10);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int quad = warp & 3, wq = warp >> 2;
-    const int m = quad * 32 + lane;
 
     if (tid == 0) {
-        mbar_init(mbar, 1);
+        for (int i = 0; i < 3; ++i) {
+            mbar_init(afree + i, 1);
+            mbar_init(afull + i, RP_COPY_WARPS);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(dfull + i, 1);
+            mbar_init(dfree + i, RP_SCATTER_WARPS);
+        }
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -281,123 +320,30 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = *tmem_holder;
-    const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
     constexpr uint32_t idesc = instr_desc(128, P, !FP16) | (1u << 15);  // A MN-major
     const uint32_t sA_addr = smem_u32(sA), sB_addr = smem_u32(sB);
-    const uint32_t srow_addr = smem_u32(srow);
     const uint32_t SBO_B = 16u * (uint32_t)KR;
     const int ntiles = (int)((Nc + 127) / 128);
-    const int nq = KR / 16;                 // copies per thread per tile
     const Scales sc = scales(*p.amax, FP16, p.wscale, p.gbound, p.nexc_c);
     const float inv_fx = 1.f / sc.fx;
     const uint32_t absent = (uint32_t)Nc;
-    uint32_t phase = 0;
 
-    // this thread's 16-byte copies: piece/K-group u = (tid >> 7) + 4 i, entry
-    // (u mod KR/8) * 8 + (tid & 7), column group (tid >> 3) & 15
-    const int eo = tid & 7, grp = (tid >> 3) & 15;
-    int64_t srcoff[MAXQ];
-    uint32_t dstoff[MAXQ];
+    // scatter geometry (warps 0-15): used chunks of 8 slots, full chunks per
+    // warp, and the remainder shared out two slots at a time
+    const int quad = warp & 3, wq = (warp >> 2) & 3;
+    const int m = quad * 32 + lane;
+    const int nchr = (p.NS + 7) / 8;
+    const int nfull = nchr / 4;
+    const int rem = nchr - 4 * nfull;                      // 0..3 chunks -> 2 rem slots per warp
+    const int tail0 = nfull * 32 + wq * 2 * rem;           // first remainder slot of this warp
 
-    auto copies = [&](int t) {
-        const int64_t j0 = (int64_t)t * 128;
-        const uint32_t st = sA_addr + (uint32_t)(t & 1) * 2u * a_piece;
-#pragma unroll
-        for (int i = 0; i < MAXQ; ++i) {
-            if (i < nq) {
-                const int u = (tid >> 7) + 4 * i;
-                const uint16_t* base = u < KR / 8 ? p.Xh : p.Xl;
-                const bool ok = srcoff[i] >= 0;
-                const uint16_t* src = ok ? base + srcoff[i] + j0 : base;
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(st + dstoff[i]),
-                             "l"(src), "r"(ok ? 16u : 0u) : "memory");
-            }
-        }
-        cp_async_commit();
-    };
-
-    auto issue = [&](int t) {
-        const uint32_t st = sA_addr + (uint32_t)(t & 1) * 2u * a_piece;
-        const uint32_t d = tbase;
-        const int ksteps = KR / 16;
-#pragma unroll
-        for (int pass = 0; pass < NW + 1; ++pass) {
-            // pass 0: A_hi B_0, pass 1: A_lo B_0, pass j+1 (j >= 1): A_hi B_j
-            const uint32_t a = st + (pass == 1 ? a_piece : 0u);
-            const int piece = pass <= 1 ? 0 : pass - 1;
-            const uint32_t bb = sB_addr + (uint32_t)piece * b_piece;
-            for (int j = 0; j < ksteps; ++j) {
-                const uint64_t ad = smem_desc(a + (uint32_t)j * 2u * A_LBO, A_LBO, A_SBO);
-                const uint64_t bd = smem_desc(bb + (uint32_t)(j * 256), 128u, SBO_B);
-                mma_ss(d, ad, bd, idesc, (pass | j) != 0);
-            }
-        }
-        mma_commit(mbar);
-    };
-
-    constexpr int NLD = NFULL + (HALF ? 1 : 0);
-    auto load_d = [&](uint32_t (&dr)[NLD][8]) {
-        const uint32_t dcol = tbase + lane_base;
-#pragma unroll
-        for (int k = 0; k < NFULL; ++k) tmem_ld8(dcol + (uint32_t)((wq + 4 * k) * 8), dr[k]);
-        if (HALF) {
-            const uint32_t c = (uint32_t)((NFULL * 4 + (wq >> 1)) * 8 + (wq & 1) * 4);
-            tmem_ld4(dcol + c, dr[NLD - 1]);
-        }
-        tmem_ld_wait();
-    };
-
-    auto load_words = [&](int t, uint32_t (&w)[NLD][4]) {
-        const int64_t jc = (int64_t)t * 128 + m;
-        const int64_t jcc = jc < Nc ? jc : Nc - 1;
-#pragma unroll
-        for (int k = 0; k < NFULL; ++k) {
-            const uint4 v = __ldg(p.tslot8 + (int64_t)(wq + 4 * k) * Nc + jcc);
-            w[k][0] = v.x; w[k][1] = v.y; w[k][2] = v.z; w[k][3] = v.w;
-        }
-        if (HALF) {
-            const uint2* q = reinterpret_cast<const uint2*>(
-                p.tslot8 + (int64_t)(NFULL * 4 + (wq >> 1)) * Nc + jcc);
-            const uint2 v = __ldg(q + (wq & 1));
-            w[NLD - 1][0] = v.x; w[NLD - 1][1] = v.y;
-        }
-    };
-
-    auto scatter = [&](int t, const uint32_t (&dr)[NLD][8], const uint32_t (&w)[NLD][4]) {
-        const bool valid = (int64_t)t * 128 + m < Nc;
-#pragma unroll
-        for (int k = 0; k < NLD; ++k) {
-            const int nu = (HALF && k == NLD - 1) ? 4 : 8;
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                if (u < nu) {
-                    const uint32_t ww = w[k][u >> 1];
-                    // entry u: tgt | sign << 15 in half u & 1 of word u >> 1
-                    const uint32_t tg = (u & 1) ? (ww >> 16) & 0x7FFFu : ww & 0x7FFFu;
-                    const uint32_t sg = (u & 1) ? (ww & 0x80000000u) : (ww << 16) & 0x80000000u;
-                    const int q = __float2int_rn(__uint_as_float(dr[k][u] ^ sg));
-                    if (valid && tg != absent) atom_add_shared(srow_addr + tg * 4u, q);
-                }
-            }
-        }
-    };
-
-    auto wait_mma = [&]() {
-        if (tid == 0) {
-            long long t0 = clock64();
-            while (!mbar_try_wait(mbar, phase)) {
-                if (clock64() - t0 > WAIT_CYCLES) {
-                    *abort_flag = 1;
-                    atomicExch(p.err, 1);
-                    break;
-                }
-            }
-        }
-        phase ^= 1u;
-    };
+    // tiles processed by this CTA over all rows: tile g uses A stage g % nst
+    // (the k-th use of a stage completes its barriers' phase k, parity k & 1)
+    // and D buffer g & 1
+    uint32_t g = 0;
 
     for (int64_t ir = blockIdx.x; ir < p.Nr; ir += gridDim.x) {
-        // row set-up: zero sigma; the row's source rows, slots and signs
+        // ---- row set-up: zero sigma; the row's source rows, slots and signs; B_R
         for (int64_t j = tid; j <= Nc; j += RP_THREADS) srow[j] = 0;
         for (int e = tid; e < RP_MAXK; e += RP_THREADS) {
             const bool in = e < p.rnexc;
@@ -405,18 +351,6 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
             rsl[e] = in ? p.rslot[ir * p.rnexc + e] : (uint16_t)0xFFFFu;
         }
         __syncthreads();
-#pragma unroll
-        for (int i = 0; i < MAXQ; ++i) {
-            if (i < nq) {
-                const int u = (tid >> 7) + 4 * i;
-                const int kc = u % (KR / 8), piece = u / (KR / 8);
-                const int64_t ro = rowoff[kc * 8 + eo];
-                srcoff[i] = ro >= 0 ? ro + 8 * grp : -1;
-                dstoff[i] = (uint32_t)piece * a_piece + (uint32_t)grp * A_SBO +
-                            (uint32_t)kc * A_LBO + (uint32_t)eo * 16u;
-            }
-        }
-        // B_R[s][e] = sgn_e W_piece[slot(e)][s] bscale (canonical K-major layout)
 #pragma unroll 1
         for (int piece = 0; piece < NW; ++piece) {
             const uint16_t* wsrc = p.wrow + (size_t)piece * P * P;
@@ -435,39 +369,198 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
             }
         }
         fence_proxy_async_smem();
-
-        // tiles (stage t & 1 holds tile t's A from copies(t) until MMA(t) is done)
-        copies(0);
-        if (ntiles > 1) copies(1); else cp_async_commit();
-        cp_async_wait<1>();
-        fence_proxy_async_smem();
-        tc_fence_before();
         __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            issue(0);
-        }
-        for (int t = 0; t < ntiles; ++t) {
-            uint32_t w[NLD][4];
-            load_words(t, w);
-            wait_mma();
-            __syncthreads();
-            if (*abort_flag) break;
-            tc_fence_after();
-            uint32_t dr[NLD][8];
-            load_d(dr);
-            if (t + 2 < ntiles) copies(t + 2); else cp_async_commit();
-            cp_async_wait<1>();
-            fence_proxy_async_smem();
-            tc_fence_before();
-            __syncthreads();
-            if (t + 1 < ntiles && tid == 0) {
-                tc_fence_after();
-                issue(t + 1);
+
+        if (warp >= RP_SCATTER_WARPS && warp < RP_MMA_WARP) {
+            // ---- copies: (piece, K-group) pairs u < KR / 4, u = cw + RP_COPY_WARPS i
+            // for copy warp cw; per pair this lane copies entry kc * 8 + (lane & 7),
+            // column groups (lane >> 3) + 4 v, v < 4
+            constexpr int MAXU = (RP_MAXK / 4 + RP_COPY_WARPS - 1) / RP_COPY_WARPS;
+            const int cw = warp - RP_SCATTER_WARPS;
+            const int eo = lane & 7, g0 = lane >> 3;
+            const int nu = KR / 4, kpg = KR / 8;
+            int32_t so[MAXU];                       // element offset in the piece, -1: padding
+#pragma unroll
+            for (int i = 0; i < MAXU; ++i) {
+                const int u = cw + RP_COPY_WARPS * i;
+                so[i] = -1;
+                if (u < nu) {
+                    const int kc = u < kpg ? u : u - kpg;
+                    const int64_t ro = rowoff[kc * 8 + eo];
+                    so[i] = ro >= 0 ? (int32_t)ro + 8 * g0 : -1;
+                }
             }
-            scatter(t, dr, w);
+            auto copies = [&](int t, uint32_t stage) {
+                const int32_t j0 = t * 128;
+                const uint32_t st = sA_addr + stage * 2u * a_piece + (uint32_t)g0 * A_SBO +
+                                    (uint32_t)eo * 16u;
+#pragma unroll
+                for (int i = 0; i < MAXU; ++i) {
+                    const int u = cw + RP_COPY_WARPS * i;
+                    if (u < nu) {
+                        const bool lo = u >= kpg;
+                        const int kc = lo ? u - kpg : u;
+                        const uint16_t* base = lo ? p.Xl : p.Xh;
+                        const bool ok = so[i] >= 0;
+                        const uint16_t* src = base + (ok ? so[i] + j0 : 0);
+                        const uint32_t dst = st + (lo ? a_piece : 0u) + (uint32_t)kc * A_LBO;
+                        const uint32_t nb = ok ? 16u : 0u;
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) {
+                            // column groups g0 + 4 v: 32 elements apart in x, 4 core matrices in A
+                            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                                         ::"r"(dst + (uint32_t)v * 4u * A_SBO),
+                                         "l"(src + (ok ? 32 * v : 0)), "r"(nb) : "memory");
+                        }
+                    }
+                }
+                cp_async_commit();
+            };
+            // copies of tile gi have landed: make them visible to the tensor core
+            auto publish = [&](uint32_t gi, bool newest_pending) {
+                if (newest_pending) cp_async_wait<1>(); else cp_async_wait<0>();
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(afull + gi % nst);
+            };
+            bool ok = true;
+            for (int t = 0; t < ntiles && ok; ++t) {
+                const uint32_t gt = g + (uint32_t)t;
+                if (gt >= nst) {
+                    // stage gt % nst is free once MMA(gt - nst) has completed
+                    if (lane == 0)
+                        ok = wait_phase(afree + gt % nst, (gt / nst - 1) & 1u, abort_flag, p.err);
+                    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+                    if (!ok) break;
+                }
+                copies(t, gt % nst);
+                if (t >= 1) publish(gt - 1, true);
+            }
+            if (ok && ntiles > 0) publish(g + (uint32_t)ntiles - 1, false);
+            cp_async_wait<0>();
+        } else if (warp == RP_MMA_WARP) {
+            // ---- MMAs (one thread)
+            if (lane == 0) {
+                const int ksteps = KR / 16;
+                const uint64_t bdesc0 = smem_desc(sB_addr, 128u, SBO_B);
+                for (int t = 0; t < ntiles; ++t) {
+                    const uint32_t gi = g + (uint32_t)t;
+                    const uint32_t sg = gi % nst;
+                    const uint32_t st = sA_addr + sg * 2u * a_piece;
+                    const uint32_t d = tbase + (gi & 1u) * (uint32_t)P;
+                    if (!wait_phase(afull + sg, (gi / nst) & 1u, abort_flag, p.err)) break;
+                    if (gi >= 2 && !wait_phase(dfree + (gi & 1u), ((gi >> 1) - 1) & 1u,
+                                               abort_flag, p.err))
+                        break;
+                    tc_fence_after();
+                    // descriptor address fields advance by (bytes >> 4): K step = 2 K-groups
+                    // of A (2 * A_LBO bytes) and 256 bytes of B
+                    const uint64_t a_hi = smem_desc(st, A_LBO, A_SBO);
+                    const uint64_t a_lo = a_hi + (a_piece >> 4);
+#pragma unroll
+                    for (int pass = 0; pass < NW + 1; ++pass) {
+                        // pass 0: A_hi B_0, pass 1: A_lo B_0, pass j+1 (j >= 1): A_hi B_j
+                        const uint64_t ad0 = pass == 1 ? a_lo : a_hi;
+                        const uint64_t bd0 = bdesc0 + (uint64_t)((pass <= 1 ? 0 : pass - 1) *
+                                                                 (b_piece >> 4));
+#pragma unroll
+                        for (int j = 0; j < RP_MAXK / 16; ++j) {
+                            if (j < ksteps)
+                                mma_ss(d, ad0 + (uint64_t)(j * (2 * A_LBO >> 4)),
+                                       bd0 + (uint64_t)(j * 16), idesc, (pass | j) != 0);
+                        }
+                    }
+                    mma_commit(afree + sg);
+                    mma_commit(dfull + (gi & 1u));
+                }
+            }
+            __syncwarp();
+        } else {
+            // ---- scatter
+            uint32_t w[MAXF][4], wt[3];
+            auto load_words = [&](int t) {
+                const int64_t jc = (int64_t)t * 128 + m;
+                const int64_t jcc = jc < Nc ? jc : Nc - 1;
+#pragma unroll
+                for (int k = 0; k < MAXF; ++k) {
+                    if (k < nfull) {
+                        const uint4 v = __ldg(p.tslot8 + (int64_t)(wq + 4 * k) * Nc + jcc);
+                        w[k][0] = v.x; w[k][1] = v.y; w[k][2] = v.z; w[k][3] = v.w;
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    if (i < rem) {
+                        const int s0 = tail0 + 2 * i;      // even: a pair within one chunk
+                        const uint32_t* q = reinterpret_cast<const uint32_t*>(
+                            p.tslot8 + (int64_t)(s0 >> 3) * Nc + jcc);
+                        wt[i] = __ldg(q + ((s0 & 7) >> 1));
+                    }
+                }
+            };
+            // one present slot: sigma[tgt] += sign * round(D); tg == Nc marks an absent slot
+            auto add = [&](uint32_t word, int half, uint32_t dbits, bool valid) {
+                const uint32_t tg = half ? (word >> 16) & 0x7FFFu : word & 0x7FFFu;
+                const uint32_t sg = half ? (word & 0x80000000u) : (word << 16) & 0x80000000u;
+                const int q = __float2int_rn(__uint_as_float(dbits ^ sg));
+                if (valid && tg != absent) atomicAdd(srow + tg, q);
+            };
+            bool ok = true;
+            if (ntiles > 0) load_words(0);
+            for (int t = 0; t < ntiles && ok; ++t) {
+                const uint32_t gt = g + (uint32_t)t;
+                if (lane == 0)
+                    ok = wait_phase(dfull + (gt & 1u), (gt >> 1) & 1u, abort_flag, p.err);
+                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t dcol = tbase + ((uint32_t)(quad * 32) << 16) +
+                                      (gt & 1u) * (uint32_t)P;
+                uint32_t dr[MAXF][8], dt[6];
+#pragma unroll
+                for (int k = 0; k < MAXF; ++k)
+                    if (k < nfull) tmem_ld8(dcol + (uint32_t)((wq + 4 * k) * 8), dr[k]);
+                // remainder: pairs of slots (tail0 is even; 4-aligned when rem == 2)
+                if (rem == 2) {
+                    uint32_t r4[8];
+                    tmem_ld4(dcol + (uint32_t)tail0, r4);
+                    dt[0] = r4[0]; dt[1] = r4[1]; dt[2] = r4[2]; dt[3] = r4[3];
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 3; ++i)
+                        if (i < rem) tmem_ld2(dcol + (uint32_t)(tail0 + 2 * i), dt[2 * i], dt[2 * i + 1]);
+                }
+                tmem_ld_wait();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(dfree + (gt & 1u));
+                // this tile's words; start loading the next tile's
+                uint32_t cw[MAXF][4], ct[3];
+#pragma unroll
+                for (int k = 0; k < MAXF; ++k)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) cw[k][i] = w[k][i];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) ct[i] = wt[i];
+                if (t + 1 < ntiles) load_words(t + 1);
+                const bool valid = (int64_t)t * 128 + m < Nc;
+#pragma unroll
+                for (int k = 0; k < MAXF; ++k) {
+                    if (k < nfull) {
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) add(cw[k][u >> 1], u & 1, dr[k][u], valid);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    if (i < rem) {
+                        add(ct[i], 0, dt[2 * i], valid);
+                        add(ct[i], 1, dt[2 * i + 1], valid);
+                    }
+                }
+            }
         }
-        cp_async_wait<0>();
+        g += (uint32_t)ntiles;
         __syncthreads();
         if (*abort_flag) break;
         for (int64_t j = tid; j < Nc; j += RP_THREADS) p.Y[ir * Nc + j] = (float)srow[j] * inv_fx;
@@ -574,19 +667,19 @@ __global__ void k_split_rows_bf16(const float* __restrict__ src, int64_t R, int6
 }
 
 uint32_t tmem_cols(int P) {
-    uint32_t need = (uint32_t)P, c = 32;
+    uint32_t need = (uint32_t)(2 * P), c = 32;
     while (c < need) c <<= 1;
     return c;
 }
 
-size_t rowpass_smem(int P, int NW, int KR, int64_t Nc) {
-    return (size_t)4 * KR * 256 + (size_t)2 * NW * P * KR + 4 * (size_t)(Nc + 1) + 16 +
-           10 * RP_MAXK + 16 + 64;
+size_t rowpass_smem(int P, int NW, int KR, int64_t Nc, int nst) {
+    return (size_t)2 * nst * KR * 256 + (size_t)2 * NW * P * KR + 4 * (size_t)(Nc + 1) + 16 +
+           10 * RP_MAXK + 16 + 10 * 8 + 16;
 }
 
 template <int P>
 void* rowpass_fn(bool fp16) {
-    return fp16 ? (void*)k_rowpass<P, true, 3> : (void*)k_rowpass<P, false, 2>;
+    return fp16 ? (void*)k_rowpass<P, true, 2> : (void*)k_rowpass<P, false, 2>;
 }
 
 void* rowpass_kernel(int P, bool fp16) {
@@ -618,7 +711,7 @@ void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
     nsb = B.ns;
     dim = nsa * nsb;
     fp16 = use_fp16;
-    nw = fp16 ? 3 : 2;
+    nw = 2;
     kernel = rowpass_kernel(P, fp16);
     KR = ((A.nexc + 15) / 16) * 16;
     if (!kernel || KR > RP_MAXK || A.ns > 32766 || B.ns > 32766)
@@ -632,7 +725,14 @@ void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
     nsm = prop.multiProcessorCount;
     gbound = (float)(wcolsum * (1.0 + 1e-6));
     int64_t ncmax = nsa > nsb ? nsa : nsb;
-    smem_bytes = rowpass_smem(P, nw, KR, ncmax);
+    // three A stages where they fit (the copies of a tile then have two MMA
+    // durations to land), else two
+    nst = 3;
+    smem_bytes = rowpass_smem(P, nw, KR, ncmax, nst);
+    if (smem_bytes > (size_t)prop.sharedMemPerBlockOptin) {
+        nst = 2;
+        smem_bytes = rowpass_smem(P, nw, KR, ncmax, nst);
+    }
     // at least ~116 KB so that exactly one CTA (and one TMEM allocation) fits per SM
     size_t floor_bytes = 116 * 1024;
     if (smem_bytes < floor_bytes) smem_bytes = floor_bytes;
@@ -715,7 +815,7 @@ void TcSigma::apply(const float* x, float* y, int ncol, cudaStream_t st) {
         // opposite-spin part: rows alpha, columns beta; writes Y
         RowPass p1{xh, xl, xp, Y, nsa, nsb, slot_b.as<uint4>(),
                    ta->tgt.as<int32_t>(), rslot_a.as<uint16_t>(), ta->nexc, KR,
-                   wimg.as<uint16_t>(), nc, am, wscale, gbound, tb->nexc, err.as<int>()};
+                   wimg.as<uint16_t>(), nc, am, wscale, gbound, tb->nexc, NS, nst, err.as<int>()};
         int g1 = (int)(nsa < nsm ? nsa : nsm);
         void* args1[] = {&p1};
         KPM_CUDA(cudaLaunchKernel(kernel, dim3(g1), dim3(RP_THREADS), args1, smem_bytes, st));

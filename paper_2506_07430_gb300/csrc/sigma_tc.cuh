@@ -13,7 +13,7 @@ struct TcSigma {
     int64_t nsa = 0, nsb = 0, dim = 0;
     int nsm = 0;                  // SMs of the device (persistent grid)
     bool fp16 = false;            // operand format: split FP16 (scaled) or split BF16
-    int nw = 2;                   // 16-bit pieces of W (3 for FP16, 2 for BF16)
+    int nw = 2;                   // 16-bit pieces of W
     float wscale = 1.0f;          // power-of-two scale of W in the image
     float gbound = 0.0f;          // max over output slots of sum over input slots of |W|
     void* kernel = nullptr;       // k_rowpass instantiation for P
@@ -26,6 +26,7 @@ struct TcSigma {
     DenseSS dense;                // same-spin parts (dense GEMMs with F_a, F_b)
     DevBuf err;                   // int error flag (1: a bounded wait ran out)
     DevBuf amax;                  // max |x| (float bits): operand scale, fixed-point range
+    int nst = 2;                  // A stages of the row pass (3 where shared memory allows)
     size_t smem_bytes = 0;
 
     // wmax: max |W| over (pq|rs) and k_pq (host-computed), for the FP16 scale;
