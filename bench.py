@@ -37,9 +37,10 @@ import synthetic  # noqa: E402
 METRIC = "Chebyshev steps/s at 16o/16e"
 UNIT = "steps/s"
 
-# DRAM bytes per H application measured by ncu for the dominant kernel, per
-# launch; None until a capture of the current kernel exists.
-NCU_TRAFFIC_BYTES = {}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# dominant kernel, from one ncu capture of the current kernel (summarised in
+# profiles/k_rowpass_fci16o16e.md); absent (null) where no capture exists.
+NCU_TRAFFIC_BYTES = {("fci16o16e", "mixed"): 12.3798e9 + 0.65982e9}
 
 
 def parse_args():
@@ -254,6 +255,7 @@ def run_ours(args, ws, rank, local, pg):
     l0 = launch_count()
     k.profile_enable(True)
     k.profile_read()
+    k.profile_read_rowpass()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
@@ -264,6 +266,7 @@ def run_ours(args, ws, rank, local, pg):
     launches = launch_count() - l0
     ms = e0.elapsed_time(e1)
     sig_ms, sig_cnt = k.profile_read()
+    rp_ms, rp_cnt = k.profile_read_rowpass()
     k.profile_enable(False)
     clk = clocks.stop()
     barrier(pg)
@@ -274,28 +277,40 @@ def run_ours(args, ws, rank, local, pg):
     mom = k.recursion_moments()
     moments_ok = bool(np.all(np.abs(mom) <= mom[:, :1] * (1 + 1e-6)))
 
-    # roofline of the dominant kernel (the H application)
+    # roofline of the dominant kernel: the opposite-spin row pass (k_rowpass) on
+    # the tensor-core paths, the gather kernel (the whole H application) otherwise
     peaks, peak_src = measured_peaks()
     nexc = na * (n - na + 1)
+    nexc_b = nb * (n - nb + 1)
     nnbr = same_spin_neighbours(n, na)
-    flops = step_flops(w, nexc, nnbr)
-    per_launch_s = (sig_ms / max(sig_cnt, 1)) / 1e3
-    achieved = flops / per_launch_s / 1e12
+    flops_h = step_flops(w, nexc, nnbr)
+    sig_launch_s = (sig_ms / max(sig_cnt, 1)) / 1e3
+    hbm_floor_ms = round(12.0 * dim / (float(peaks.get("hbm_gbs", 6776.6)) * 1e9) * 1e3, 4)
     if args.precision in ("mixed", "mixed_bf16"):
+        flops = 2.0 * nexc * nexc_b * dim          # opposite-spin contraction, one FMA per pair
+        per_launch_s = (rp_ms / max(rp_cnt, 1)) / 1e3
         bound, peak = "tensor", float(peaks.get("bf16_tflops_sustained", 1735.0))
-        peak_note = f"bf16 dense sustained, {peak_src}"
+        peak_note = f"bf16 dense sustained (FP16 same rate), {peak_src}"
+        kname, share = "k_rowpass (opposite-spin two-electron term, tcgen05)", rp_ms / ms
     else:
+        flops = flops_h
+        per_launch_s = sig_launch_s
         bound = "alu"
         peak = alu_peak_tflops(args.precision, float(peaks.get("sm_max_mhz", 2070.0)))
         peak_note = ("FP32 CUDA cores 152 SM x 128 lanes x 2 x max clock" if args.precision == "fp32"
                      else "GB300 FP64 1.25 TFLOP/s")
+        kname, share = "H application (k_sigma_gather)", sig_ms / ms
+    achieved = flops / per_launch_s / 1e12
     roof = {"bound": bound, "achieved": round(achieved, 4), "peak": round(peak, 2),
             "unit": "TFLOP/s", "frac": round(achieved / peak, 6),
             "traffic": NCU_TRAFFIC_BYTES.get((args.workload, args.precision)),
-            "kernel": "H application (sigma)", "peak_source": peak_note,
+            "kernel": kname, "peak_source": peak_note,
             "algorithmic_flops_per_launch": flops,
-            "launch_ms": round(per_launch_s * 1e3, 4), "launch_share": round(sig_ms / ms, 4),
-            "hbm_floor_ms": round(12.0 * dim / (float(peaks.get("hbm_gbs", 6776.6)) * 1e9) * 1e3, 4)}
+            "launch_ms": round(per_launch_s * 1e3, 4), "launch_share": round(share, 4),
+            "h_application": {"ms": round(sig_launch_s * 1e3, 4), "share": round(sig_ms / ms, 4),
+                              "algorithmic_flops": flops_h,
+                              "tflops": round(flops_h / sig_launch_s / 1e12, 4),
+                              "hbm_floor_ms": hbm_floor_ms}}
 
     # end to end through the C-ABI with host buffers: psi0 from pinned host memory
     # H2D, dipole, recursion, moments D2H, per request
@@ -320,7 +335,7 @@ def run_ours(args, ws, rank, local, pg):
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": steps,
         "warmup": warm, "ms_per_step": round(ms_max / steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "fp16x(2,3)-f32acc",
+        "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "fp16x(2,2)-f32acc",
                   "mixed_bf16": "bf16x2-f32acc"}[args.precision],
         "data": "synthetic (seeded integrals, seeded normalised state in place of the NQS ground state)",
         "config": {"workload": args.workload, "norb": n, "nalpha": na, "nbeta": nb, "dim": dim,

@@ -223,6 +223,18 @@ kpm_status kpm_profile_enable(kpm_ctx* ctx, int enable);
 kpm_status kpm_profile_read(kpm_ctx* ctx, double* sigma_ms, int* count);
 
 /*
+ * kpm_profile_read_rowpass -- device time of the opposite-spin tensor-core
+ * kernel (the row pass, the largest part of a KPM_MIXED / KPM_MIXED_BF16 H
+ * application) while profiling is enabled: summed milliseconds over the
+ * row-pass launches since the previous read, and their number; both reset.
+ * The launches are bracketed by CUDA event pairs on the context's stream (no
+ * extra synchronisation inside the recursion); the call synchronises the
+ * stream.  FP64 / FP32 contexts have no row pass: *rowpass_ms = 0, *count = 0.
+ * Errors: KPM_EINVAL for a NULL context, KPM_ECUDA for a CUDA failure.
+ */
+kpm_status kpm_profile_read_rowpass(kpm_ctx* ctx, double* rowpass_ms, int* count);
+
+/*
  * kpm_spectrum_static -- kpm_spectrum for callers that cannot allocate device
  * memory.  The paper has no counterpart; this entry point exists for callers
  * that cannot call cudaMalloc: processes whose device memory is entirely

@@ -40,6 +40,7 @@ SIGNATURES = {
     "kpm_synchronize": (_I, [_P]),
     "kpm_profile_enable": (_I, [_P, _I]),
     "kpm_profile_read": (_I, [_P, _P, _P]),
+    "kpm_profile_read_rowpass": (_I, [_P, _P, _P]),
     "kpm_spectrum_static": (_I, [_P, _I, _D, _D, _I, _I, _P, _P, _P]),
     "kpm_server_create": (_I, [_P, _P]),
     "kpm_server_submit": (_I, [_P, _P, _P]),
@@ -245,6 +246,13 @@ class KPM:
         """(summed ms, count) of H applications since the last read."""
         ms, cnt = ctypes.c_double(), ctypes.c_int()
         _check(self._lib().kpm_profile_read(self._h, ctypes.byref(ms), ctypes.byref(cnt)), self._h)
+        return ms.value, cnt.value
+
+    def profile_read_rowpass(self):
+        """(summed ms, count) of tensor-core row-pass launches since the last read."""
+        ms, cnt = ctypes.c_double(), ctypes.c_int()
+        _check(self._lib().kpm_profile_read_rowpass(self._h, ctypes.byref(ms), ctypes.byref(cnt)),
+               self._h)
         return ms.value, cnt.value
 
     def recursion_moments(self):

@@ -523,7 +523,20 @@ kpm_status kpm_synchronize(kpm_ctx* ctx) {
 kpm_status kpm_profile_enable(kpm_ctx* ctx, int enable) {
     if (!ctx) { g_err = "NULL context"; return KPM_EINVAL; }
     ctx->prof = enable != 0;
+    if (ctx->tc) ctx->tc->prof = ctx->prof;
     return KPM_OK;
+}
+
+kpm_status kpm_profile_read_rowpass(kpm_ctx* ctx, double* ms, int* count) {
+    if (!ctx) { g_err = "NULL context"; return KPM_EINVAL; }
+    return guarded(ctx, [&] {
+        DeviceGuard g(ctx->device);
+        double t = 0.0;
+        int n = 0;
+        if (ctx->tc) t = ctx->tc->read_prof(ctx->st, &n);
+        if (ms) *ms = t;
+        if (count) *count = n;
+    });
 }
 
 kpm_status kpm_profile_read(kpm_ctx* ctx, double* ms, int* count) {

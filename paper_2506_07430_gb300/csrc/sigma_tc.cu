@@ -818,11 +818,42 @@ void TcSigma::apply(const float* x, float* y, int ncol, cudaStream_t st) {
                    wimg.as<uint16_t>(), nc, am, wscale, gbound, tb->nexc, NS, nst, err.as<int>()};
         int g1 = (int)(nsa < nsm ? nsa : nsm);
         void* args1[] = {&p1};
+        if (prof) {
+            if ((int)ev.size() < ev_used + 2) {
+                cudaEvent_t e0, e1;
+                KPM_CUDA(cudaEventCreate(&e0));
+                KPM_CUDA(cudaEventCreate(&e1));
+                ev.push_back(e0);
+                ev.push_back(e1);
+            }
+            KPM_CUDA(cudaEventRecord(ev[ev_used], st));
+        }
         KPM_CUDA(cudaLaunchKernel(kernel, dim3(g1), dim3(RP_THREADS), args1, smem_bytes, st));
         KPM_LAUNCHED();
+        if (prof) {
+            KPM_CUDA(cudaEventRecord(ev[ev_used + 1], st));
+            ev_used += 2;
+        }
         // same-spin parts (dense GEMMs) and the exact diagonal, added into Y
         dense.apply(X, Y, am, st);
     }
+}
+
+double TcSigma::read_prof(cudaStream_t st, int* count) {
+    KPM_CUDA(cudaStreamSynchronize(st));
+    double tot = 0.0;
+    for (int i = 0; i + 1 < ev_used; i += 2) {
+        float t = 0.f;
+        KPM_CUDA(cudaEventElapsedTime(&t, ev[i], ev[i + 1]));
+        tot += t;
+    }
+    if (count) *count = ev_used / 2;
+    ev_used = 0;
+    return tot;
+}
+
+TcSigma::~TcSigma() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
 }
 
 int TcSigma::check(cudaStream_t st) {

@@ -3,6 +3,8 @@
 #include "common.cuh"
 #include "gemm_tc.cuh"
 
+#include <vector>
+
 namespace kpm {
 
 // sigma = H x with the two-electron terms contracted on the 5th-generation
@@ -37,6 +39,15 @@ struct TcSigma {
     void apply(const float* x, float* y, int ncol, cudaStream_t st);
     // Reads and clears the device error flag (synchronises the stream).
     int check(cudaStream_t st);
+
+    // Row-pass timing: while prof is set, every row-pass launch is bracketed by
+    // a CUDA event pair on the launch stream; read_prof synchronises the stream,
+    // returns the summed device time (ms) and launch count, and resets both.
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;
+    int ev_used = 0;
+    double read_prof(cudaStream_t st, int* count);
+    ~TcSigma();
 };
 
 }  // namespace kpm
