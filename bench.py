@@ -58,6 +58,19 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--sigma-only", type=int, default=0,
                    help="time this many H applications (kpm_sigma) and exit; for profiling")
+    p.add_argument("--serving", action="store_true",
+                   help="serving workload: continuous-batching MIXED server vs plain FP64 "
+                        "one request at a time (spectra/s, p50/p99 latency)")
+    p.add_argument("--serve-requests", type=int, default=64, help="requests in the served stream")
+    p.add_argument("--plain-requests", type=int, default=8,
+                   help="requests of the stream (in order, up to --plain-max-norb orbitals) "
+                        "also run plain (FP64, one at a time)")
+    p.add_argument("--plain-max-norb", type=int, default=12)
+    p.add_argument("--serve-slots", type=int, default=8)
+    p.add_argument("--accuracy", type=int, default=0, metavar="NMOMENTS",
+                   help="per-moment error of --precision (and fp32) against the FP64 path on "
+                        "--workload for NMOMENTS moments, dipole component z")
+    p.add_argument("--serve-budget-gb", type=float, default=8.0)
     return p.parse_args()
 
 
@@ -414,10 +427,176 @@ def run_sigma_only(args):
     k.close()
 
 
+def run_accuracy(args):
+    """Moments of one seeded request on --workload in FP64 (the reference: its parity
+    with the oracle is tested at 8o-12o and on sampled rows at 14o-18o) and in the
+    reduced precisions; per-moment error |dOmega_n| / Omega_0 and the relative L2
+    error of the Jackson-damped spectrum on 2048 Chebyshev nodes."""
+    import torch
+
+    from paper_2506_07430_gb300 import KPM, spectrum
+
+    torch.cuda.set_device(0)
+    w = synthetic.workload(args.workload)
+    n, na, nb = w["norb"], w["nalpha"], w["nbeta"]
+    I = synthetic.integrals(n, na, nb, w["seed"])
+    nm = int(args.accuracy)
+    psi = None
+    out = {"metric": "per-moment error vs the FP64 path", "config": {
+        "workload": args.workload, "nmoments": nm, "component": "z",
+        "state": "seeded normalised random state"}}
+    ref = None
+    for prec in ["fp64", "fp32", args.precision]:
+        if prec in out:
+            continue
+        k = KPM(I.h1, I.eri, I.dipole, n, na, nb, precision=prec)
+        if psi is None:
+            psi = torch.from_numpy(synthetic.random_state(k.dim, 2506000)).cuda()
+            emin, emax = k.bounds(iters=args.lanczos, seed=2506001)
+            a, b = KPM.scale(emin, emax)
+            out["config"].update(a=a, b=b)
+        t0 = time.perf_counter()
+        mom = k.moments(psi, 0b100, a, b, nm, check_bounds=False)[0]
+        dt = time.perf_counter() - t0
+        k.close()
+        om, it = spectrum(mom, a, b, 2048)
+        if ref is None:
+            ref = (mom, it)
+            out["fp64"] = {"seconds": round(dt, 3), "omega0": float(mom[0])}
+            continue
+        err = np.abs(mom - ref[0]) / abs(ref[0][0])
+        marks = sorted(set([min(x, nm - 1) for x in (1, 15, 63, 255, 1023, nm - 1) if x < nm]))
+        out[prec] = {"seconds": round(dt, 3),
+                     "max_moment_err_over_omega0": float(err.max()),
+                     "moment_err_at": {str(i): float(err[:i + 1].max()) for i in marks},
+                     "spectrum_rel_l2": float(np.linalg.norm(it - ref[1]) / np.linalg.norm(ref[1]))}
+    return out
+
+
+def _percentile(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = (len(xs) - 1) * q
+    f = math.floor(k)
+    c = min(f + 1, len(xs) - 1)
+    return xs[f] + (xs[c] - xs[f]) * (k - f)
+
+
+def run_serving(args):
+    """Serving workload: a stream of spectrum requests (sizes 10o/12o/14o, 512-2048
+    moments, x/y/z dipole components as one 3-column block), all submitted at t = 0.
+    Served: the continuous-batching server (several resident requests, interleaved
+    rounds of Chebyshev steps) in KPM_MIXED over the whole stream, and in KPM_MIXED
+    and KPM_FP32 over a subset; plain: KPM_FP64, one request at a time (max_slots =
+    1), over the same subset, with the whole stream extrapolated from measured FP64
+    step times.  Inputs (integrals, a seeded
+    normalised state in place of each request's ground state, and a, b from the
+    library's Lanczos bounds) are prepared before timing."""
+    import torch
+
+    from paper_2506_07430_gb300 import KPM, Server
+
+    torch.cuda.set_device(0)
+    reqs = synthetic.serving_stream(args.serve_requests, rate_hz=None)
+    prep = []
+    for r in reqs:
+        n, m = r["norb"], r["nalpha"]
+        I = synthetic.integrals(n, m, m, r["seed"])
+        k = KPM(I.h1, I.eri, I.dipole, n, m, m, precision="mixed")
+        emin, emax = k.bounds(iters=args.lanczos, seed=r["seed"])
+        a, b = KPM.scale(emin, emax)
+        psi = synthetic.random_state(k.dim, r["seed"] + 7)
+        k.close()
+        prep.append((r, I, psi, a, b))
+    torch.cuda.synchronize()
+
+    def serve(items, precision, slots):
+        srv = Server(mem_budget_bytes=int(args.serve_budget_gb * (1 << 30)), max_slots=slots,
+                     steps_per_round=16, precision=precision)
+        t0 = time.perf_counter()
+        ids = [srv.submit(I.h1, I.eri, I.dipole, r["norb"], r["nalpha"], r["nbeta"], psi, 0b111,
+                          a, b, r["nmoments"], npoints=2048)
+               for r, I, psi, a, b in items]
+        res = [srv.wait(i, timeout_ms=3600 * 1000, allow_ebounds=True) for i in ids]
+        t1 = time.perf_counter()
+        srv.close()
+        lat = [x["t_total_s"] for x in res]
+        return res, {"requests": len(items), "seconds": round(t1 - t0, 3),
+                     "spectra_per_s": round(len(items) / (t1 - t0), 4),
+                     "p50_latency_s": round(_percentile(lat, 0.5), 4),
+                     "p99_latency_s": round(_percentile(lat, 0.99), 4),
+                     "statuses": sorted(set(int(x["status"]) for x in res))}
+
+    sub = [x for x in prep if x[0]["norb"] <= args.plain_max_norb][:args.plain_requests]
+    served_all, s_all = serve(prep, "mixed", args.serve_slots)
+    plain_sub, p_sub = serve(sub, "fp64", 1)
+    subset = {}
+    for prec in ("mixed", "fp32"):
+        res, st = serve(sub, prec, args.serve_slots)
+        # accuracy of the served results against plain FP64, request by request
+        mom_err, spec_err = [], []
+        for rs, rp in zip(res, plain_sub):
+            om0 = np.abs(rp["moments"][:, :1])
+            mom_err.append(float(np.max(np.abs(rs["moments"] - rp["moments"]) / om0)))
+            spec_err.append(float(np.linalg.norm(rs["intensity"] - rp["intensity"])
+                                  / np.linalg.norm(rp["intensity"])))
+        st["max_moment_err_over_omega0"] = max(mom_err)
+        st["max_spectrum_rel_l2"] = max(spec_err)
+        st["speedup_vs_plain"] = round(st["spectra_per_s"] / p_sub["spectra_per_s"], 3)
+        subset[prec] = st
+
+    # plain FP64 time of the whole stream, extrapolated from the measured time of a
+    # Chebyshev step (3 columns) per size
+    step_s = {}
+    for r, I, psi, a, b in prep:
+        key = r["norb"]
+        if key in step_s:
+            continue
+        k = KPM(I.h1, I.eri, I.dipole, r["norb"], r["nalpha"], r["nbeta"], precision="fp64")
+        k.recursion_begin(torch.from_numpy(psi).cuda(), 0b111, a, b, 2 * 12)
+        k.recursion_advance(2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        k.recursion_advance(8)
+        k.synchronize()
+        step_s[key] = (time.perf_counter() - t0) / 8
+        k.close()
+    plain_est = sum(step_s[r["norb"]] * (r["nmoments"] // 2) for r in reqs)
+    sizes = {}
+    for r in reqs:
+        key = f"{r['norb']}o"
+        sizes[key] = sizes.get(key, 0) + 1
+    return {
+        "metric": "spectra/s, served (continuous batching) vs plain (FP64, one at a time); value: "
+                  "served FP32 (within the accuracy target) on the subset",
+        "value": subset["fp32"]["spectra_per_s"], "unit": "spectra/s", "n_gpus": 1,
+        "higher_is_better": True, "vs_baseline": None, "data": "synthetic",
+        "config": {"workload": "serving stream (10o/12o/14o, 512-2048 moments, x/y/z block, "
+                               "all arrivals at t=0)",
+                   "sizes": sizes, "slots": args.serve_slots,
+                   "budget_gb": args.serve_budget_gb, "steps_per_round": 16},
+        "served_stream_mixed": s_all,
+        "plain_subset_fp64": p_sub,
+        "served_subset": subset,
+        "subset": f"first {len(sub)} requests of the stream with <= {args.plain_max_norb} orbitals",
+        "accuracy_target": {"moment_err_over_omega0": 1e-6, "spectrum_rel_l2": 1e-4},
+        "plain_fp64_step_s": {f"{k}o": round(v, 6) for k, v in step_s.items()},
+        "plain_stream_seconds_extrapolated": round(plain_est, 2),
+        "speedup_stream_extrapolated_mixed": round(plain_est / s_all["seconds"], 3),
+    }
+
+
 def main():
     args = parse_args()
     if args.sigma_only:
         run_sigma_only(args)
+        return
+    if args.serving:
+        print(json.dumps(run_serving(args)), flush=True)
+        return
+    if args.accuracy:
+        print(json.dumps(run_accuracy(args)), flush=True)
         return
     if args.impl == "reference":
         # rank 0 alone times the oracle; other ranks exit without work
