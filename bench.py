@@ -470,6 +470,31 @@ def run_accuracy(args):
                      "max_moment_err_over_omega0": float(err.max()),
                      "moment_err_at": {str(i): float(err[:i + 1].max()) for i in marks},
                      "spectrum_rel_l2": float(np.linalg.norm(it - ref[1]) / np.linalg.norm(ref[1]))}
+
+    # error of one H application by term: full H, one-body only (ERI = 0), two-body
+    # only (diagonal h); relative 2-norm error against FP64 on a random state
+    cases = {"full": (I.h1, I.eri), "onebody": (I.h1, np.zeros_like(I.eri)),
+             "twobody": (np.diag(np.diag(I.h1)), I.eri)}
+    by_term = {}
+    for name, (h1, eri) in cases.items():
+        k = KPM(h1, eri, I.dipole, n, na, nb, precision="fp64")
+        x = torch.from_numpy(synthetic.random_state(k.dim, 7)).cuda()
+        y = torch.empty_like(x)
+        k.sigma(x, y)
+        k.synchronize()
+        ref_y = y.cpu().numpy()
+        k.close()
+        by_term[name] = {}
+        for prec in ("fp32", args.precision):
+            k = KPM(h1, eri, I.dipole, n, na, nb, precision=prec)
+            xs = x.float()
+            ys = torch.empty_like(xs)
+            k.sigma(xs, ys)
+            k.synchronize()
+            d = ys.double().cpu().numpy() - ref_y
+            by_term[name][prec] = float(np.linalg.norm(d) / np.linalg.norm(ref_y))
+            k.close()
+    out["sigma_rel_err_by_term"] = by_term
     return out
 
 

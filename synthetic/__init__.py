@@ -104,6 +104,8 @@ WORKLOADS = {
                     npoints=2048, ncol=3, precision="fp64"),
     "fci12o12e": dict(norb=12, nalpha=6, nbeta=6, seed=2506072, nmoments=1024,
                       npoints=2048, ncol=3, precision="fp32"),
+    "fci14o14e": dict(norb=14, nalpha=7, nbeta=7, seed=2506074, nmoments=1024,
+                      npoints=2048, ncol=3, precision="mixed"),
     "fci16o16e": dict(norb=16, nalpha=8, nbeta=8, seed=2506073, nmoments=2048,
                       npoints=2048, ncol=1, precision="mixed"),
     "fci18o18e": dict(norb=18, nalpha=9, nbeta=9, seed=2506075, nmoments=1024,
