@@ -308,6 +308,55 @@ def test_sigma_mixed_full(torch, prec, n, na, nb):
 
 
 @pytest.mark.parametrize("prec", MIXED)
+def test_sigma_mixed_fixed_point_range(torch, prec):
+    """A state whose values align every term of one opposite-spin sum, so that
+    row's fixed-point sum reaches a large part of the a-priori range of the
+    scatter (more than a quarter of it): the integer accumulation must neither
+    overflow nor lose the small terms elsewhere."""
+    n, na, nb, seed = 8, 4, 4, 2506071
+    I, sc = _sc(n, na, nb, seed=seed)
+    masks, tgt, pq, sgn = ostr.excitation_table(n, na)
+    nexc = pq.shape[1]
+
+    def slot(v):
+        p, q = divmod(int(v), n)
+        return max(p, q) * (max(p, q) + 1) // 2 + min(p, q)
+
+    nsl = n * (n + 1) // 2
+    W = np.zeros((nsl, nsl))
+    for p in range(n):
+        for q in range(n):
+            for r in range(n):
+                for s in range(n):
+                    W[slot(p * n + q), slot(r * n + s)] = I.eri[p, q, r, s]
+    R0 = 14
+    coef = {}
+    for e in range(nexc):
+        for f in range(nexc):
+            key = (int(tgt[R0, e]), int(tgt[R0, f]))
+            coef[key] = coef.get(key, 0.0) + sgn[R0, e] * sgn[R0, f] * W[slot(pq[R0, e]),
+                                                                            slot(pq[R0, f])]
+    N = len(masks)
+    x = 1e-3 * synthetic.random_state(N * N, 11) * math.sqrt(N * N)
+    X = x.reshape(N, N)
+    for (a, b), c in coef.items():
+        X[a, b] = 1.0 if c >= 0 else -1.0
+    # the aligned sum against the a-priori bound of the fixed-point scale
+    aligned = sum(abs(c) for c in coef.values())
+    bound = 1.02 * nexc * 1.0 * np.abs(W).sum(axis=0).max()
+    assert aligned > bound / 4, (aligned, bound)
+    x = X.reshape(-1).astype(np.float32)
+    k = _kpm(I, n, na, nb, prec)
+    y = k.sigma(torch.tensor(x[None, :], device="cuda")).cpu().numpy()[0]
+    k.synchronize()
+    ref = sc.sigma(x.astype(np.float64))
+    err = np.abs(y - ref).max() / np.abs(ref).max()
+    print(prec, "aligned-sum state: sigma error / max|y|:", err)
+    assert err < MIXED_TOL[prec], err
+    k.close()
+
+
+@pytest.mark.parametrize("prec", MIXED)
 @pytest.mark.parametrize("n,na,nb", [(14, 7, 7), (16, 8, 8)])
 def test_sigma_mixed_sampled_rows(torch, prec, n, na, nb):
     w = {14: 2506150, 16: 2506073}[n]
