@@ -67,6 +67,9 @@ def parse_args():
                         "also run plain (FP64, one at a time)")
     p.add_argument("--plain-max-norb", type=int, default=12)
     p.add_argument("--serve-slots", type=int, default=8)
+    p.add_argument("--graphs-compare", type=int, default=0, metavar="NSTEPS",
+                   help="time NSTEPS Chebyshev steps of --workload/--precision with the steps "
+                        "replayed from CUDA graphs and issued kernel by kernel")
     p.add_argument("--accuracy", type=int, default=0, metavar="NMOMENTS",
                    help="per-moment error of --precision (and fp32) against the FP64 path on "
                         "--workload for NMOMENTS moments, dipole component z")
@@ -427,6 +430,49 @@ def run_sigma_only(args):
     k.close()
 
 
+def run_graphs_compare(args):
+    """Chebyshev steps/s on --workload with the recursion steps replayed from CUDA
+    graphs (the default) and issued kernel by kernel; inputs resident, no
+    profiling; 3 warm-up chunks, then the timed steps."""
+    import torch
+
+    from paper_2506_07430_gb300 import KPM
+
+    torch.cuda.set_device(0)
+    w = synthetic.workload(args.workload)
+    n, na, nb = w["norb"], w["nalpha"], w["nbeta"]
+    I = synthetic.integrals(n, na, nb, w["seed"])
+    nsteps = int(args.graphs_compare)
+    out = {"metric": "Chebyshev steps/s, graph replay vs direct launches",
+           "config": {"workload": args.workload, "precision": args.precision,
+                      "ncol": w["ncol"], "steps": nsteps}}
+    for graphs in (True, False):
+        k = KPM(I.h1, I.eri, I.dipole, n, na, nb, precision=args.precision)
+        k.graphs_enable(graphs)
+        psi = torch.from_numpy(synthetic.random_state(k.dim, 2506000)).cuda()
+        emin, emax = k.bounds(iters=args.lanczos, seed=2506001)
+        a, b = KPM.scale(emin, emax)
+        mask = 0b111 if w["ncol"] == 3 else 0b100
+        k.recursion_begin(psi, mask, a, b, 2 * (nsteps + 64 + 1))
+        for _ in range(3):
+            k.recursion_advance(16)
+        k.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record()
+        k.recursion_advance(nsteps)
+        e1.record()
+        k.synchronize()
+        wall = time.perf_counter() - t0
+        ms = e0.elapsed_time(e1)
+        out["graphs" if graphs else "direct"] = {
+            "steps_per_s": round(nsteps / (ms / 1e3), 2), "us_per_step": round(1e3 * ms / nsteps, 3),
+            "host_wall_s": round(wall, 4)}
+        k.close()
+    out["speedup"] = round(out["graphs"]["steps_per_s"] / out["direct"]["steps_per_s"], 3)
+    return out
+
+
 def run_accuracy(args):
     """Moments of one seeded request on --workload in FP64 (the reference: its parity
     with the oracle is tested at 8o-12o and on sampled rows at 14o-18o) and in the
@@ -622,6 +668,9 @@ def main():
         return
     if args.accuracy:
         print(json.dumps(run_accuracy(args)), flush=True)
+        return
+    if args.graphs_compare:
+        print(json.dumps(run_graphs_compare(args)), flush=True)
         return
     if args.impl == "reference":
         # rank 0 alone times the oracle; other ranks exit without work

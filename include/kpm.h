@@ -212,6 +212,18 @@ kpm_status kpm_spectrum(const double* moments, int nmoments, double a, double b,
 kpm_status kpm_synchronize(kpm_ctx* ctx);
 
 /*
+ * kpm_graphs_enable -- kpm_recursion_advance (and kpm_moments, the server)
+ * issue pairs of Chebyshev steps as replays of CUDA graphs captured on first
+ * use (one per assignment of the two rotating recursion vectors; the step
+ * index is kept on the device), which removes the per-kernel launch cost that
+ * dominates small problems.  Enabled by default; enable = 0 issues every kernel
+ * directly.  Results are identical either way (same kernels, same arguments).
+ * Steps run directly while profiling is enabled, and for good if a capture
+ * fails.  Errors: KPM_EINVAL for a NULL context.
+ */
+kpm_status kpm_graphs_enable(kpm_ctx* ctx, int enable);
+
+/*
  * Per-launch timing of the H application inside the recursion.
  * kpm_profile_enable(ctx, 1): every H application queued by later
  * kpm_recursion_advance calls on ctx is bracketed by a CUDA event pair recorded

@@ -41,6 +41,7 @@ SIGNATURES = {
     "kpm_profile_enable": (_I, [_P, _I]),
     "kpm_profile_read": (_I, [_P, _P, _P]),
     "kpm_profile_read_rowpass": (_I, [_P, _P, _P]),
+    "kpm_graphs_enable": (_I, [_P, _I]),
     "kpm_spectrum_static": (_I, [_P, _I, _D, _D, _I, _I, _P, _P, _P]),
     "kpm_server_create": (_I, [_P, _P]),
     "kpm_server_submit": (_I, [_P, _P, _P]),
@@ -238,6 +239,9 @@ class KPM:
 
     def synchronize(self):
         _check(self._lib().kpm_synchronize(self._h), self._h)
+
+    def graphs_enable(self, on: bool = True):
+        _check(self._lib().kpm_graphs_enable(self._h, 1 if on else 0), self._h)
 
     def profile_enable(self, on: bool = True):
         _check(self._lib().kpm_profile_enable(self._h, 1 if on else 0), self._h)

@@ -44,8 +44,25 @@ struct kpm_ctx {
     std::vector<cudaEvent_t> ev;
     int ev_used = 0;
 
+    // recursion steps replayed from CUDA graphs of two steps, one graph per
+    // assignment of the two rotating vectors; the step index lives on the device
+    bool graphs = true;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    uint64_t glaunches[2] = {0, 0};   // kernels in one replay (launch accounting)
+    DevBuf step_ctr;                  // unsigned: index n of the next step's dots
+    cudaStream_t cap_st = nullptr;    // private stream for capture (any user stream may be
+                                      // the legacy default stream, which cannot be captured)
+    void drop_graphs() {
+        for (auto& g : gexec) {
+            if (g) cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    }
+
     ~kpm_ctx() {
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        drop_graphs();
+        if (cap_st) cudaStreamDestroy(cap_st);
     }
 
     size_t esz() const { return prec == KPM_FP64 ? 8 : 4; }
@@ -139,16 +156,16 @@ void dipole_dispatch(kpm_ctx* c, int comp, const double* psi, void* y) {
 }
 
 void update_dispatch(kpm_ctx* c, const void* s, const void* cur, void* prev, int first,
-                     double* dots_at) {
+                     double* dots, const unsigned* step) {
     int64_t dstride = (int64_t)c->rec_max_steps * 2;
     if (c->prec == KPM_FP64)
         cheb_update_f64((const double*)s, (const double*)cur, (double*)prev, c->dim, c->rec_ncol,
                         c->rec_a, c->rec_b, first, c->partials.as<double>(),
-                        c->counters.as<unsigned>(), dots_at, dstride, c->st);
+                        c->counters.as<unsigned>(), dots, dstride, step, c->st);
     else
         cheb_update_f32((const float*)s, (const float*)cur, (float*)prev, c->dim, c->rec_ncol,
                         c->rec_a, c->rec_b, first, c->partials.as<double>(),
-                        c->counters.as<unsigned>(), dots_at, dstride, c->st);
+                        c->counters.as<unsigned>(), dots, dstride, step, c->st);
 }
 
 void ensure_reduce_scratch(kpm_ctx* c, int ncol) {
@@ -186,36 +203,103 @@ void rec_begin(kpm_ctx* c, const double* psi0, unsigned mask, double a, double b
         ++j;
     }
     sigma_dispatch(c, c->vB.p, c->vS.p, ncol);
-    update_dispatch(c, c->vS.p, c->vB.p, c->vA.p, 1, c->dots.as<double>());
+    update_dispatch(c, c->vS.p, c->vB.p, c->vA.p, 1, c->dots.as<double>(), nullptr);
     c->rec_prev = c->vB.p;  // alpha_0
     c->rec_cur = c->vA.p;   // alpha_1
     c->rec_steps = 1;
+    // buffers may have moved: captured steps are stale
+    c->drop_graphs();
+    c->step_ctr.ensure(sizeof(unsigned));
+    step_set(c->step_ctr.as<unsigned>(), 1u, c->st);
+}
+
+// one Chebyshev step alpha_{n+1} = 2 (H~ alpha_n) - alpha_{n-1}, dots of step n
+void step_direct(kpm_ctx* c) {
+    if (c->prof) {
+        if ((int)c->ev.size() < c->ev_used + 2) {
+            cudaEvent_t e0, e1;
+            KPM_CUDA(cudaEventCreate(&e0));
+            KPM_CUDA(cudaEventCreate(&e1));
+            c->ev.push_back(e0);
+            c->ev.push_back(e1);
+        }
+        KPM_CUDA(cudaEventRecord(c->ev[c->ev_used], c->st));
+        sigma_dispatch(c, c->rec_cur, c->vS.p, c->rec_ncol);
+        KPM_CUDA(cudaEventRecord(c->ev[c->ev_used + 1], c->st));
+        c->ev_used += 2;
+    } else {
+        sigma_dispatch(c, c->rec_cur, c->vS.p, c->rec_ncol);
+    }
+    update_dispatch(c, c->vS.p, c->rec_cur, c->rec_prev, 0, c->dots.as<double>(),
+                    c->step_ctr.as<unsigned>());
+    step_inc(c->step_ctr.as<unsigned>(), c->st);
+    std::swap(c->rec_prev, c->rec_cur);
+    ++c->rec_steps;
+}
+
+// Captures two steps from the current vector assignment into graph slot gi, on
+// the context's private capture stream; host state is restored (capture
+// executes nothing).  Returns false, with graphs disabled for the context, if
+// the capture fails.
+bool capture_two_steps(kpm_ctx* c, int gi) {
+    if (!c->cap_st && cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        c->cap_st = nullptr;
+        c->graphs = false;
+        return false;
+    }
+    void* cur0 = c->rec_cur;
+    void* prev0 = c->rec_prev;
+    const int steps0 = c->rec_steps;
+    const uint64_t l0 = g_launches.load();
+    cudaStream_t user_st = c->st;
+    cudaGraph_t graph = nullptr;
+    c->st = c->cap_st;
+    bool ok = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        try {
+            step_direct(c);
+            step_direct(c);
+        } catch (...) {
+            ok = false;
+        }
+        ok = (cudaStreamEndCapture(c->st, &graph) == cudaSuccess) && ok && graph;
+    }
+    c->st = user_st;
+    if (ok) ok = cudaGraphInstantiate(&c->gexec[gi], graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    c->glaunches[gi] = g_launches.load() - l0;
+    g_launches.fetch_sub(c->glaunches[gi]);
+    c->rec_cur = cur0;
+    c->rec_prev = prev0;
+    c->rec_steps = steps0;
+    if (!ok) {
+        cudaGetLastError();
+        c->gexec[gi] = nullptr;
+        c->graphs = false;
+    }
+    return ok;
 }
 
 void rec_advance(kpm_ctx* c, int nsteps) {
     if (c->rec_steps <= 0) KPM_THROW(KPM_EINVAL, "no recursion in progress");
     if (nsteps < 0 || c->rec_steps + nsteps > c->rec_max_steps)
         KPM_THROW(KPM_EINVAL, "advance past the requested number of moments");
-    for (int k = 0; k < nsteps; ++k) {
-        if (c->prof) {
-            if ((int)c->ev.size() < c->ev_used + 2) {
-                cudaEvent_t e0, e1;
-                KPM_CUDA(cudaEventCreate(&e0));
-                KPM_CUDA(cudaEventCreate(&e1));
-                c->ev.push_back(e0);
-                c->ev.push_back(e1);
+    int k = 0;
+    while (k < nsteps) {
+        if (c->graphs && !c->prof && nsteps - k >= 2) {
+            // two steps leave the two rotating vectors where they were
+            const int gi = c->rec_cur == c->vA.p ? 0 : 1;
+            if (c->gexec[gi] || capture_two_steps(c, gi)) {
+                KPM_CUDA(cudaGraphLaunch(c->gexec[gi], c->st));
+                g_launches.fetch_add(c->glaunches[gi]);
+                c->rec_steps += 2;
+                k += 2;
+                continue;
             }
-            KPM_CUDA(cudaEventRecord(c->ev[c->ev_used], c->st));
-            sigma_dispatch(c, c->rec_cur, c->vS.p, c->rec_ncol);
-            KPM_CUDA(cudaEventRecord(c->ev[c->ev_used + 1], c->st));
-            c->ev_used += 2;
-        } else {
-            sigma_dispatch(c, c->rec_cur, c->vS.p, c->rec_ncol);
         }
-        update_dispatch(c, c->vS.p, c->rec_cur, c->rec_prev, 0,
-                        c->dots.as<double>() + 2 * (int64_t)c->rec_steps);
-        std::swap(c->rec_prev, c->rec_cur);
-        ++c->rec_steps;
+        step_direct(c);
+        ++k;
     }
 }
 
@@ -537,6 +621,13 @@ kpm_status kpm_profile_read_rowpass(kpm_ctx* ctx, double* ms, int* count) {
         if (ms) *ms = t;
         if (count) *count = n;
     });
+}
+
+kpm_status kpm_graphs_enable(kpm_ctx* ctx, int enable) {
+    if (!ctx) { g_err = "NULL context"; return KPM_EINVAL; }
+    ctx->graphs = enable != 0;
+    if (!ctx->graphs) ctx->drop_graphs();
+    return KPM_OK;
 }
 
 kpm_status kpm_profile_read(kpm_ctx* ctx, double* ms, int* count) {

@@ -140,12 +140,18 @@ int reduce_blocks(int64_t dim);
 
 // alpha_next = first ? (s - b c)/a : 2 (s - b c)/a - prev, written over prev;
 // dots[col*stride + 0] = <c|c>, dots[col*stride + 1] = <next|c> (FP64).
+// dots of the step go to dots[2n], dots[2n+1] (per column, stride dots_col_stride),
+// n = *step when step is non-null (device counter), else n = 0 at `dots`.
 void cheb_update_f64(const double* s, const double* c, double* prev, int64_t dim, int ncol,
                      double a, double b, int first, double* partials, unsigned* counters,
-                     double* dots, int64_t dots_col_stride, cudaStream_t st);
+                     double* dots, int64_t dots_col_stride, const unsigned* step,
+                     cudaStream_t st);
 void cheb_update_f32(const float* s, const float* c, float* prev, int64_t dim, int ncol,
                      double a, double b, int first, double* partials, unsigned* counters,
-                     double* dots, int64_t dots_col_stride, cudaStream_t st);
+                     double* dots, int64_t dots_col_stride, const unsigned* step,
+                     cudaStream_t st);
+void step_set(unsigned* step, unsigned v, cudaStream_t st);
+void step_inc(unsigned* step, cudaStream_t st);
 
 // moments[col][2n], [2n+1] from dots[col][n][2] (doubling identities).
 void doubling_combine(const double* dots, int ncol, int nsteps, int64_t dots_col_stride,

@@ -83,8 +83,10 @@ template <class T>
 __global__ void __launch_bounds__(RED_THREADS)
 k_cheb_update(const T* __restrict__ s, const T* __restrict__ c, T* __restrict__ prev, int64_t dim,
               double a, double b, int first, double* partials, unsigned* counters, double* dots,
-              int64_t dstride) {
+              int64_t dstride, const unsigned* step) {
     const int col = blockIdx.y;
+    // dots of step n go to dots[2n], dots[2n+1]; n from the device counter if given
+    if (step) dots += 2 * (int64_t)(*step);
     s += col * dim;
     c += col * dim;
     prev += col * dim;
@@ -129,22 +131,38 @@ k_cheb_update(const T* __restrict__ s, const T* __restrict__ c, T* __restrict__ 
 template <class T>
 static void launch_update(const T* s, const T* c, T* prev, int64_t dim, int ncol, double a,
                           double b, int first, double* partials, unsigned* counters, double* dots,
-                          int64_t dstride, cudaStream_t st) {
+                          int64_t dstride, const unsigned* step, cudaStream_t st) {
     dim3 grid(reduce_blocks(dim), ncol);
     k_cheb_update<T><<<grid, RED_THREADS, 0, st>>>(s, c, prev, dim, a, b, first, partials,
-                                                   counters, dots, dstride);
+                                                   counters, dots, dstride, step);
     KPM_LAUNCHED();
 }
 
 void cheb_update_f64(const double* s, const double* c, double* prev, int64_t dim, int ncol,
                      double a, double b, int first, double* partials, unsigned* counters,
-                     double* dots, int64_t dstride, cudaStream_t st) {
-    launch_update<double>(s, c, prev, dim, ncol, a, b, first, partials, counters, dots, dstride, st);
+                     double* dots, int64_t dstride, const unsigned* step, cudaStream_t st) {
+    launch_update<double>(s, c, prev, dim, ncol, a, b, first, partials, counters, dots, dstride,
+                          step, st);
 }
 void cheb_update_f32(const float* s, const float* c, float* prev, int64_t dim, int ncol, double a,
                      double b, int first, double* partials, unsigned* counters, double* dots,
-                     int64_t dstride, cudaStream_t st) {
-    launch_update<float>(s, c, prev, dim, ncol, a, b, first, partials, counters, dots, dstride, st);
+                     int64_t dstride, const unsigned* step, cudaStream_t st) {
+    launch_update<float>(s, c, prev, dim, ncol, a, b, first, partials, counters, dots, dstride,
+                         step, st);
+}
+
+__global__ void k_step_set(unsigned* step, unsigned v) { *step = v; }
+__global__ void k_step_inc(unsigned* step) { *step += 1u; }
+
+// device-side step counter of the recursion (read by k_cheb_update), so that a
+// captured step is replayable
+void step_set(unsigned* step, unsigned v, cudaStream_t st) {
+    k_step_set<<<1, 1, 0, st>>>(step, v);
+    KPM_LAUNCHED();
+}
+void step_inc(unsigned* step, cudaStream_t st) {
+    k_step_inc<<<1, 1, 0, st>>>(step);
+    KPM_LAUNCHED();
 }
 
 __global__ void k_doubling(const double* __restrict__ dots, int nsteps, int64_t dstride,

@@ -426,3 +426,25 @@ def test_sigma_18_orbitals_sampled_rows(torch):
     got = y[torch.tensor(rows, device="cuda")].cpu().numpy().astype(np.float64)
     assert np.abs(got - ref).max() / np.abs(ref).max() < 2e-6
     k.close()
+
+
+@pytest.mark.parametrize("prec,n,ne", [("fp64", 8, 4), ("fp32", 10, 5), ("mixed", 10, 5)])
+def test_graph_steps_equal_direct_steps(torch, prec, n, ne):
+    """Recursion steps replayed from captured CUDA graphs give the same moments,
+    bit for bit, as the same steps issued kernel by kernel (chunk sizes mix graph
+    replays and single steps, and both vector assignments)."""
+    I = synthetic.integrals(n, ne, ne, 2506200 + n)
+    out = []
+    for graphs in (True, False):
+        k = _kpm(I, n, ne, ne, prec)
+        k.graphs_enable(graphs)
+        psi = torch.from_numpy(synthetic.random_state(k.dim, 5)).cuda()
+        emin, emax = k.bounds(iters=40, seed=3)
+        a, b = k.scale(emin, emax)
+        k.recursion_begin(psi, 0b101, a, b, 2 * 40)
+        for chunk in (3, 2, 7, 1, 6, 4, 5, 11):
+            k.recursion_advance(chunk)
+        out.append(k.recursion_moments())
+        k.close()
+    assert out[0].shape == (2, 80)
+    assert np.array_equal(out[0], out[1])
