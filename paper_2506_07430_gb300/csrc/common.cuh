@@ -93,6 +93,7 @@ struct SpinTables {
     DevBuf masks;            // uint32 [ns]
     DevBuf tgt, pq, sgn;     // int32/uint16/int8 [ns][nexc]  (API layout)
     DevBuf tgtT, pqT, sgnT;  // int32/uint16/int8 [nexc][ns]  (string-fastest, coalesced)
+    DevBuf pkT;              // uint32 [nexc][ns]: target | pq << 16 | (sign < 0) << 31
     DevBuf fcol;             // int32  [nnbr][ns]  same-spin string Hamiltonian columns
     DevBuf fval64;           // double [nnbr][ns]
     DevBuf fval32;           // float  [nnbr][ns]

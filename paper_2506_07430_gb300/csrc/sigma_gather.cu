@@ -205,10 +205,59 @@ k_dipole(const double* __restrict__ psi, T* __restrict__ y, int64_t nsa, int64_t
     y[ia * nsb + ib] = (T)(-acc);
 }
 
+// One block per alpha row I_a: the row psi[I_a][:] is staged in shared memory,
+// so the beta terms (targets within the row) are read there; the alpha terms
+// read whole rows psi[J_a][:] (coalesced across the block's threads).  Beta
+// entries come from the packed table, 4 bytes per term.
+template <class T>
+__global__ void __launch_bounds__(256)
+k_dipole_rows(const double* __restrict__ psi, T* __restrict__ y, int64_t nsb,
+              const int32_t* __restrict__ tgtA, const uint16_t* __restrict__ pqA,
+              const int8_t* __restrict__ sgnA, int nexcA, const uint32_t* __restrict__ pkB,
+              int nexcB, const double* __restrict__ d, int nn) {
+    extern __shared__ double sd[];
+    double* row = sd;                                    // [nsb]
+    double* cA = row + nsb;                              // [nexcA] signed coefficients
+    int64_t* oA = reinterpret_cast<int64_t*>(cA + nexcA);  // [nexcA] row offsets
+    double* dd = reinterpret_cast<double*>(oA + nexcA);  // [nn] dipole integrals
+    const int64_t ia = blockIdx.x;
+    for (int64_t j = threadIdx.x; j < nsb; j += blockDim.x) row[j] = psi[ia * nsb + j];
+    for (int i = threadIdx.x; i < nn; i += blockDim.x) dd[i] = d[i];
+    for (int e = threadIdx.x; e < nexcA; e += blockDim.x) {
+        const int64_t k = ia * nexcA + e;
+        cA[e] = d[pqA[k]] * (double)sgnA[k];
+        oA[e] = (int64_t)tgtA[k] * nsb;
+    }
+    __syncthreads();
+    for (int64_t ib = threadIdx.x; ib < nsb; ib += blockDim.x) {
+        double acc = 0.0;
+        for (int e = 0; e < nexcA; ++e) acc += cA[e] * psi[oA[e] + ib];
+        for (int f = 0; f < nexcB; ++f) {
+            const uint32_t w = pkB[(int64_t)f * nsb + ib];
+            const double c = dd[(w >> 16) & 0x7FFFu];
+            acc += ((w >> 31) ? -c : c) * row[w & 0xFFFFu];
+        }
+        y[ia * nsb + ib] = (T)(-acc);
+    }
+}
+
 template <class T>
 static void launch_dipole(const SpinTables& A, const SpinTables& B, const double* d,
                           const double* psi, T* y, cudaStream_t st) {
     if (A.ns * B.ns == 0) return;
+    const int nn = A.n * A.n;
+    const size_t smem = sizeof(double) * ((size_t)B.ns + 2 * (size_t)A.nexc + nn);
+    if (smem <= 200 * 1024) {
+        // per device; cheap, and the dipole runs once per request
+        KPM_CUDA(cudaFuncSetAttribute(k_dipole_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      200 * 1024));
+        k_dipole_rows<T><<<(unsigned)A.ns, 256, smem, st>>>(
+            psi, y, B.ns, A.tgt.as<int32_t>(), A.pq.as<uint16_t>(), A.sgn.as<int8_t>(), A.nexc,
+            B.pkT.as<uint32_t>(), B.nexc, d, nn);
+        KPM_LAUNCHED();
+        return;
+    }
+    // rows too long for shared memory: gather the beta terms from global memory
     dim3 grid((unsigned)((B.ns + 127) / 128), (unsigned)A.ns);
     k_dipole<T><<<grid, 128, 0, st>>>(psi, y, A.ns, B.ns, A.tgt.as<int32_t>(),
                                       A.pq.as<uint16_t>(), A.sgn.as<int8_t>(), A.nexc,

@@ -188,6 +188,15 @@ static int64_t binom64(int n, int k) {
     return r;
 }
 
+// packed transposed table: one 32-bit word per entry (targets < 2^16 for n <= 18)
+__global__ void k_pack_tables(const int32_t* __restrict__ tgtT, const uint16_t* __restrict__ pqT,
+                              const int8_t* __restrict__ sgnT, int64_t ne,
+                              uint32_t* __restrict__ pkT) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne) return;
+    pkT[i] = (uint32_t)tgtT[i] | ((uint32_t)pqT[i] << 16) | (sgnT[i] < 0 ? 0x80000000u : 0u);
+}
+
 void build_spin_tables(SpinTables& t, int n, int m, const double* d_h1, const double* d_eri,
                        cudaStream_t st) {
     t.n = n;
@@ -216,6 +225,13 @@ void build_spin_tables(SpinTables& t, int n, int m, const double* d_h1, const do
                                t.pq.as<uint16_t>(), t.sgn.as<int8_t>(), t.tgtT.as<int32_t>(),
                                t.pqT.as<uint16_t>(), t.sgnT.as<int8_t>());
     KPM_LAUNCHED();
+    t.pkT.alloc(ne * 4 + 4);
+    if (ne > 0) {
+        k_pack_tables<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
+            t.tgtT.as<int32_t>(), t.pqT.as<uint16_t>(), t.sgnT.as<int8_t>(), (int64_t)ne,
+            t.pkT.as<uint32_t>());
+        KPM_LAUNCHED();
+    }
     k_same_spin<<<bl, th, 0, st>>>(t.masks.as<uint32_t>(), n, t.ns, t.nnbr, B, d_h1, d_eri,
                                   t.fcol.as<int32_t>(), t.fval64.as<double>());
     KPM_LAUNCHED();
