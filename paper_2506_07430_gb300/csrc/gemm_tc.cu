@@ -19,8 +19,9 @@
 // float hi + lo), together with nothing else.
 //
 // Kernel: CTA tile 128 x 256, k-block 64 (128 bytes per row: one SWIZZLE_128B
-// atom row), two-stage TMA pipeline (full/empty mbarriers), one thread issues
-// TMA, one issues MMAs, four warps run the epilogue.  All waits are bounded.
+// atom row), two-stage TMA pipeline (full/empty mbarriers), one warp issues TMA,
+// one issues MMAs, eight warps drain accumulator chunks (see k_gemm) and run the
+// epilogue.  All waits are bounded.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
@@ -35,7 +36,11 @@ namespace kpm {
 namespace {
 
 constexpr int GM_BM = 128, GM_BN = 256, GM_BK = 64, GM_STAGES = 2;
-constexpr int GM_THREADS = 128;
+constexpr int GM_EPI_WARPS = 8;               // 2 per TMEM lane quadrant, 128 columns each
+constexpr int GM_TMA_WARP = GM_EPI_WARPS;       // producer (one thread)
+constexpr int GM_MMA_WARP = GM_EPI_WARPS + 1;   // MMA issue (one thread)
+constexpr int GM_THREADS = 32 * (GM_EPI_WARPS + 2);
+constexpr int GM_CHUNKS = 24;                   // target number of accumulation chunks over K
 constexpr uint32_t A_BYTES = GM_BM * GM_BK * 2;  // 16 KB per piece
 constexpr uint32_t B_BYTES = GM_BN * GM_BK * 2;  // 32 KB per piece
 constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
@@ -142,6 +147,31 @@ struct GemmArgs {
     int* err;
 };
 
+// bounded wait that also gives up when another role has aborted
+__device__ __forceinline__ bool wait_or_abort(uint64_t* b, uint32_t parity, volatile int* abort_flag,
+                                              int* err) {
+    long long t0 = clock64();
+    while (!mbar_test(b, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > GM_WAIT) {
+            *abort_flag = 1;
+            atomicExch(err, 1);
+            return false;
+        }
+    }
+    return true;
+}
+__device__ __forceinline__ void mbar_arrive_(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+
+// Accumulation in chunks: the MMA thread restarts the accumulator every ck
+// k-blocks, alternating two tensor-memory accumulators of GM_BN columns; the
+// epilogue warps add each finished chunk into FP32 running sums held in
+// registers while the next chunk accumulates.  An FP32 accumulator that takes
+// one rounding per k-step over all of K (12870 at 16 orbitals) carries an error
+// growing like sqrt(K); in chunks, each accumulator sums a short run and the
+// running sum takes one rounding per chunk.
 __global__ void __launch_bounds__(GM_THREADS, 1)
 k_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
        const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
@@ -151,11 +181,12 @@ k_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensor
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + GM_STAGES * STAGE_BYTES);
     uint64_t* empty = full + GM_STAGES;
-    uint64_t* done = empty + GM_STAGES;
-    uint32_t* holder = reinterpret_cast<uint32_t*>(done + 1);
-    int* abort_flag = reinterpret_cast<int*>(holder + 1);
-    int* issued = abort_flag + 1;     // stages whose TMA loads were issued
-    int* consumed = issued + 1;       // stages whose full barrier the MMA thread passed
+    uint64_t* accf = empty + GM_STAGES;   // [2] accumulator chunk finished
+    uint64_t* acce = accf + 2;            // [2] accumulator drained (epilogue warps)
+    uint32_t* holder = reinterpret_cast<uint32_t*>(acce + 2);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(holder + 1);
+    int* issued = const_cast<int*>(abort_flag) + 1;   // stages whose TMA loads were issued
+    int* consumed = issued + 1;                       // stages the MMA thread passed
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // grouped rasterisation: groups of GROUP_M row tiles walk all column tiles,
@@ -169,13 +200,18 @@ k_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensor
     const int m0 = (first_m + (b % gsize) % gm) * GM_BM;
     const int n0 = ((b % gsize) / gm) * GM_BN;
     const int nk = (g.K + GM_BK - 1) / GM_BK;
+    const int ck = max(2, (nk + GM_CHUNKS - 1) / GM_CHUNKS);   // k-blocks per chunk
+    const int nchunk = (nk + ck - 1) / ck;
 
     if (tid == 0) {
         for (int s = 0; s < GM_STAGES; ++s) {
             mbar_init_(&full[s], 1);
             mbar_init_(&empty[s], 1);
         }
-        mbar_init_(done, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init_(&accf[i], 1);
+            mbar_init_(&acce[i], GM_EPI_WARPS);
+        }
         *abort_flag = 0;
         *issued = 0;
         *consumed = 0;
@@ -186,7 +222,7 @@ k_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensor
         prefetch_map(&mB1);
     }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;"
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;"
                      ::"r"(su32(holder)) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -195,88 +231,113 @@ k_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensor
     tc_after();
     const uint32_t tmem = *holder;
 
-    if (tid == 0) {
-        // TMA producer
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % GM_STAGES;
-            if (kb >= GM_STAGES) {
-                if (!mbar_wait_bounded(&empty[s], ((kb / GM_STAGES) - 1) & 1, g.err)) {
-                    *abort_flag = 1;
+    if (warp == GM_TMA_WARP) {
+        if (lane == 0) {
+            // TMA producer
+            for (int kb = 0; kb < nk; ++kb) {
+                const int s = kb % GM_STAGES;
+                if (kb >= GM_STAGES &&
+                    !wait_or_abort(&empty[s], ((kb / GM_STAGES) - 1) & 1, abort_flag, g.err))
                     break;
-                }
+                unsigned char* st = smem + s * STAGE_BYTES;
+                mbar_expect_tx(&full[s], STAGE_BYTES);
+                const int kx = kb * GM_BK;
+                tma_load_2d(su32(st), &mA0, kx, m0, &full[s]);
+                tma_load_2d(su32(st + A_BYTES), &mA1, kx, m0, &full[s]);
+                tma_load_2d(su32(st + 2 * A_BYTES), &mB0, kx, n0, &full[s]);
+                tma_load_2d(su32(st + 2 * A_BYTES + B_BYTES), &mB1, kx, n0, &full[s]);
+                *(volatile int*)issued = kb + 1;
             }
-            unsigned char* st = smem + s * STAGE_BYTES;
-            mbar_expect_tx(&full[s], STAGE_BYTES);
-            const int kx = kb * GM_BK;
-            tma_load_2d(su32(st), &mA0, kx, m0, &full[s]);
-            tma_load_2d(su32(st + A_BYTES), &mA1, kx, m0, &full[s]);
-            tma_load_2d(su32(st + 2 * A_BYTES), &mB0, kx, n0, &full[s]);
-            tma_load_2d(su32(st + 2 * A_BYTES + B_BYTES), &mB1, kx, n0, &full[s]);
-            *(volatile int*)issued = kb + 1;
         }
-    } else if (tid == 32) {
-        // MMA issuer
-        constexpr uint32_t idesc = gemm_idesc();
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % GM_STAGES;
-            if (!mbar_wait_bounded(&full[s], (kb / GM_STAGES) & 1, g.err)) {
-                *abort_flag = 1;
-                break;
-            }
-            *(volatile int*)consumed = kb + 1;
-            tc_after();
-            const uint32_t st = su32(smem + s * STAGE_BYTES);
-            const uint32_t a0 = st, a1 = st + A_BYTES, b0 = st + 2 * A_BYTES,
-                           b1 = st + 2 * A_BYTES + B_BYTES;
+    } else if (warp == GM_MMA_WARP) {
+        if (lane == 0) {
+            // MMA issuer: chunk c accumulates k-blocks [c ck, (c + 1) ck) into buffer c & 1
+            constexpr uint32_t idesc = gemm_idesc();
+            for (int c = 0; c < nchunk; ++c) {
+                const uint32_t d = tmem + (uint32_t)((c & 1) * GM_BN);
+                if (c >= 2 && !wait_or_abort(&acce[c & 1], ((c >> 1) - 1) & 1, abort_flag, g.err))
+                    break;
+                tc_after();
+                const int kb1 = min(nk, (c + 1) * ck);
+                bool ok = true;
+                for (int kb = c * ck; kb < kb1; ++kb) {
+                    const int s = kb % GM_STAGES;
+                    if (!wait_or_abort(&full[s], (kb / GM_STAGES) & 1, abort_flag, g.err)) {
+                        ok = false;
+                        break;
+                    }
+                    *(volatile int*)consumed = kb + 1;
+                    tc_after();
+                    const uint32_t st = su32(smem + s * STAGE_BYTES);
+                    const uint32_t a0 = st, a1 = st + A_BYTES, b0 = st + 2 * A_BYTES,
+                                   b1 = st + 2 * A_BYTES + B_BYTES;
 #pragma unroll
-            for (int j = 0; j < GM_BK / 16; ++j) {
-                const uint32_t off = j * 32;  // 16 FP16 = 32 bytes along K in the atom row
-                const uint32_t acc0 = (kb | j) != 0;
-                mma_ss(tmem, sw128_desc(a0 + off), sw128_desc(b0 + off), idesc, acc0);
-                mma_ss(tmem, sw128_desc(a1 + off), sw128_desc(b0 + off), idesc, 1);
-                mma_ss(tmem, sw128_desc(a0 + off), sw128_desc(b1 + off), idesc, 1);
-            }
-            mma_commit_(&empty[s]);
-        }
-        mma_commit_(done);
-    }
-    __syncwarp();
-    // epilogue: every thread waits for the last MMAs
-    bool ok = mbar_wait_bounded(done, 0, g.err);
-    __syncthreads();
-    if (*abort_flag) ok = false;
-    tc_after();
-    float scale = g.scale / g.wscale;
-    if (g.amax) {
-        const float mx = *g.amax;
-        if (mx > 0.f && isfinite(mx)) {
-            int e;
-            frexpf(mx, &e);
-            scale = scale / ldexpf(1.f, 14 - max(e, -90));
-        }
-    }
-    const int m = m0 + warp * 32 + lane;
-    const bool mval = m < g.M;
-    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-    float2 dmv = make_float2(0.f, 0.f);
-    if (g.x && mval) dmv = g.dm[m];
-#pragma unroll 1
-    for (int c = 0; c < GM_BN; c += 32) {
-        uint32_t r[32];
-        ld32(trow + (uint32_t)c, r);
-        if (!ok || !mval) continue;
-#pragma unroll 8
-        for (int u = 0; u < 32; ++u) {
-            const int n = n0 + c + u;
-            if (n < g.N) {
-                const int64_t o = (int64_t)n * g.ldy + m;
-                float v = g.y[o] + __uint_as_float(r[u]) * scale;
-                if (g.x) {
-                    const float2 dn = g.dn[n];
-                    const float xv = g.x[o];
-                    v = fmaf(dmv.x + dn.x, xv, fmaf(dmv.y + dn.y, xv, v));
+                    for (int j = 0; j < GM_BK / 16; ++j) {
+                        const uint32_t off = j * 32;  // 16 FP16 = 32 bytes along K in the atom row
+                        const uint32_t acc0 = (kb != c * ck || j != 0) ? 1u : 0u;
+                        mma_ss(d, sw128_desc(a0 + off), sw128_desc(b0 + off), idesc, acc0);
+                        mma_ss(d, sw128_desc(a1 + off), sw128_desc(b0 + off), idesc, 1);
+                        mma_ss(d, sw128_desc(a0 + off), sw128_desc(b1 + off), idesc, 1);
+                    }
+                    mma_commit_(&empty[s]);
                 }
-                g.y[o] = v;
+                if (!ok) break;
+                mma_commit_(&accf[c & 1]);
+            }
+        }
+    } else {
+        // epilogue warps: running sums of columns [128 h, 128 h + 128) for row m
+        const int quad = warp & 3, h = warp >> 2;
+        const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(h * 128);
+        float rs[128];
+#pragma unroll
+        for (int u = 0; u < 128; ++u) rs[u] = 0.f;
+        bool ok = true;
+        for (int c = 0; c < nchunk && ok; ++c) {
+            if (lane == 0) ok = wait_or_abort(&accf[c & 1], (c >> 1) & 1, abort_flag, g.err);
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!ok) break;
+            tc_after();
+            const uint32_t src = trow + (uint32_t)((c & 1) * GM_BN);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t r[32];
+                ld32(src + (uint32_t)(q * 32), r);
+#pragma unroll
+                for (int u = 0; u < 32; ++u) rs[q * 32 + u] += __uint_as_float(r[u]);
+            }
+            tc_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_(&acce[c & 1]);
+        }
+        if (ok && !*abort_flag) {
+            float scale = g.scale / g.wscale;
+            if (g.amax) {
+                const float mx = *g.amax;
+                if (mx > 0.f && isfinite(mx)) {
+                    int e;
+                    frexpf(mx, &e);
+                    scale = scale / ldexpf(1.f, 14 - max(e, -90));
+                }
+            }
+            const int m = m0 + quad * 32 + lane;
+            if (m < g.M) {
+                float2 dmv = make_float2(0.f, 0.f);
+                if (g.x) dmv = g.dm[m];
+#pragma unroll
+                for (int u = 0; u < 128; ++u) {
+                    const int n = n0 + h * 128 + u;
+                    if (n < g.N) {
+                        const int64_t o = (int64_t)n * g.ldy + m;
+                        float v = g.y[o] + rs[u] * scale;
+                        if (g.x) {
+                            const float2 dn = g.dn[n];
+                            const float xv = g.x[o];
+                            v = fmaf(dmv.x + dn.x, xv, fmaf(dmv.y + dn.y, xv, v));
+                        }
+                        g.y[o] = v;
+                    }
+                }
             }
         }
     }
@@ -289,7 +350,7 @@ k_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensor
     }
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem)
                      : "memory");
 }
 

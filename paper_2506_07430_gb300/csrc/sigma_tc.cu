@@ -157,6 +157,11 @@ struct RowPass {
     int nexc_c;              // table entries per column string (contributions per target)
     int NS;                  // slots in use (n(n+1)/2); slots [NS, P) are padding
     int nst;                 // A stages in shared memory (2 or 3)
+    int shift;               // fixed-point scale = 2^shift x the a-priori one (see k_rowpass)
+    const int* rows;         // if set: process rows rows[0 .. *nrows) only
+    const int* nrows;
+    int* flagged;            // if set: rows whose range check failed are appended here
+    int* nflagged;
     int* err;
 };
 
@@ -166,6 +171,10 @@ constexpr int RP_MMA_WARP = RP_SCATTER_WARPS + RP_COPY_WARPS;   // MMA issue (on
 constexpr int RP_WARPS = RP_SCATTER_WARPS + RP_COPY_WARPS + 1;
 constexpr int RP_THREADS = 32 * RP_WARPS;
 constexpr int RP_MAXK = 96;                  // largest KR: 9 * 10 = 90 entries rounded up
+// first-pass fixed-point scale: 2^RP_SHIFT times the a-priori one (the terms of a
+// vector are normally far below the a-priori per-term bound; rows whose terms
+// come within the 32-bit headroom are redone at the a-priori scale)
+constexpr int RP_SHIFT = 3;
 constexpr uint32_t A_LBO = 2048;             // A stage: K-group (8 entries) stride, bytes
 constexpr uint32_t A_SBO = 128;              // A stage: MN-group (8 columns) stride, bytes
 
@@ -176,7 +185,7 @@ struct Scales {
     float bscale;  // W image -> B_R, so that D = value * fx
 };
 __device__ __forceinline__ Scales scales(float mx, bool fp16, float wscale, float gbound,
-                                         int nexc_c) {
+                                         int nexc_c, int shift) {
     Scales c{1.f, 1.f, 1.f};
     if (mx > 0.f && isfinite(mx)) {
         int e;
@@ -186,7 +195,7 @@ __device__ __forceinline__ Scales scales(float mx, bool fp16, float wscale, floa
         const float bound = 1.02f * (float)nexc_c * mx * gbound;
         int f = -90;
         if (bound > 0.f) frexpf(bound, &f);  // bound < 2^f
-        c.fx = ldexpf(1.f, 31 - max(f, -90));
+        c.fx = ldexpf(1.f, 31 + shift - max(f, -90));
     }
     c.bscale = c.fx / (c.sa * wscale);
     return c;
@@ -274,6 +283,14 @@ __device__ __forceinline__ bool wait_phase(uint64_t* mbar, uint32_t parity, vola
 //     warps of a quadrant share the NS used slots evenly (chunks of 8
 //     round-robin, the remaining chunks split in pairs of slots).
 // Rows are separated by CTA barriers (set-up of the next row's B_R and sigma).
+//
+// Fixed-point range: integer addition wraps, so only each final row sum has to
+// fit in 32 bits, and it does whenever every term |D| < 2^31 / nexc_c.  The
+// first launch runs at a scale 2^shift finer than the a-priori bound that
+// guarantees this; the scatter warps track max |D| per row, and a row that
+// reaches the limit is not written but appended to a list that the second
+// launch (shift = 0, rows from the list) recomputes.  Which rows take the
+// second pass depends only on the data, so results stay reproducible.
 template <int P, bool FP16, int NW>
 __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
     constexpr int MAXF = P >= 32 ? P / 32 : 1;     // full chunks per scatter warp (upper bound)
@@ -296,6 +313,7 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
     uint64_t* dfree = afree + 8;                           // [2] D buffer d read (16 warps)
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(afree + 10);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+    volatile int* range_flag = abort_flag + 1;             // this row failed the range check
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -324,8 +342,12 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
     const uint32_t sA_addr = smem_u32(sA), sB_addr = smem_u32(sB);
     const uint32_t SBO_B = 16u * (uint32_t)KR;
     const int ntiles = (int)((Nc + 127) / 128);
-    const Scales sc = scales(*p.amax, FP16, p.wscale, p.gbound, p.nexc_c);
+    const Scales sc = scales(*p.amax, FP16, p.wscale, p.gbound, p.nexc_c, p.shift);
     const float inv_fx = 1.f / sc.fx;
+    // every target receives at most nexc_c terms: if each |D| (fixed-point units)
+    // stays below this limit, every row sum fits in 32 bits
+    const float dlimit = floorf(2147483648.f / (float)p.nexc_c) - 1.f;
+    const int64_t nrows = p.rows ? (int64_t)*p.nrows : p.Nr;
     const uint32_t absent = (uint32_t)Nc;
 
     // scatter geometry (warps 0-15): used chunks of 8 slots, full chunks per
@@ -342,8 +364,10 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
     // and D buffer g & 1
     uint32_t g = 0;
 
-    for (int64_t ir = blockIdx.x; ir < p.Nr; ir += gridDim.x) {
+    for (int64_t idx = blockIdx.x; idx < nrows; idx += gridDim.x) {
+        const int64_t ir = p.rows ? (int64_t)p.rows[idx] : idx;
         // ---- row set-up: zero sigma; the row's source rows, slots and signs; B_R
+        if (tid == 0) *range_flag = 0;
         for (int64_t j = tid; j <= Nc; j += RP_THREADS) srow[j] = 0;
         for (int e = tid; e < RP_MAXK; e += RP_THREADS) {
             const bool in = e < p.rnexc;
@@ -499,9 +523,11 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
                 }
             };
             // one present slot: sigma[tgt] += sign * round(D); tg == Nc marks an absent slot
+            float dmax = 0.f;    // largest |D| this thread has seen in the row
             auto add = [&](uint32_t word, int half, uint32_t dbits, bool valid) {
                 const uint32_t tg = half ? (word >> 16) & 0x7FFFu : word & 0x7FFFu;
                 const uint32_t sg = half ? (word & 0x80000000u) : (word << 16) & 0x80000000u;
+                dmax = fmaxf(dmax, fabsf(__uint_as_float(dbits)));
                 const int q = __float2int_rn(__uint_as_float(dbits ^ sg));
                 if (valid && tg != absent) atomicAdd(srow + tg, q);
             };
@@ -559,11 +585,19 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
                     }
                 }
             }
+            if (dmax >= dlimit) *range_flag = 1;
         }
         g += (uint32_t)ntiles;
         __syncthreads();
         if (*abort_flag) break;
-        for (int64_t j = tid; j < Nc; j += RP_THREADS) p.Y[ir * Nc + j] = (float)srow[j] * inv_fx;
+        if (*range_flag && p.flagged) {
+            // a term may have pushed a row sum past 32 bits: the row is redone at
+            // the a-priori scale by the following launch
+            if (tid == 0) p.flagged[atomicAdd(p.nflagged, 1)] = (int)ir;
+        } else {
+            for (int64_t j = tid; j < Nc; j += RP_THREADS)
+                p.Y[ir * Nc + j] = (float)srow[j] * inv_fx;
+        }
         __syncthreads();
     }
     tc_fence_before();
@@ -784,6 +818,8 @@ void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
     }
     err.alloc(sizeof(int));
     amax.alloc(2 * sizeof(unsigned));
+    flagged.alloc((size_t)(nsa > 0 ? nsa : 1) * sizeof(int));
+    nflag.alloc(sizeof(int));
     KPM_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
     dense.init(A, B, &A == &B, err.as<int>(), st);
 }
@@ -812,12 +848,24 @@ void TcSigma::apply(const float* x, float* y, int ncol, cudaStream_t st) {
             xh = xbh.as<uint16_t>();
             xl = xbl.as<uint16_t>();
         }
-        // opposite-spin part: rows alpha, columns beta; writes Y
+        // opposite-spin part: rows alpha, columns beta; writes Y.  First pass at a
+        // fixed-point scale 2^RP_SHIFT finer than the a-priori one, with a range
+        // check per row; second pass redoes the rows that failed it at the a-priori
+        // scale (its row count is read on the device: no synchronisation).
+        KPM_CUDA(cudaMemsetAsync(nflag.p, 0, sizeof(int), st));
         RowPass p1{xh, xl, xp, Y, nsa, nsb, slot_b.as<uint4>(),
                    ta->tgt.as<int32_t>(), rslot_a.as<uint16_t>(), ta->nexc, KR,
-                   wimg.as<uint16_t>(), nc, am, wscale, gbound, tb->nexc, NS, nst, err.as<int>()};
+                   wimg.as<uint16_t>(), nc, am, wscale, gbound, tb->nexc, NS, nst, RP_SHIFT,
+                   nullptr, nullptr, flagged.as<int>(), nflag.as<int>(), err.as<int>()};
+        RowPass p2 = p1;
+        p2.shift = 0;
+        p2.rows = flagged.as<int>();
+        p2.nrows = nflag.as<int>();
+        p2.flagged = nullptr;
+        p2.nflagged = nullptr;
         int g1 = (int)(nsa < nsm ? nsa : nsm);
         void* args1[] = {&p1};
+        void* args2[] = {&p2};
         if (prof) {
             if ((int)ev.size() < ev_used + 2) {
                 cudaEvent_t e0, e1;
@@ -829,6 +877,8 @@ void TcSigma::apply(const float* x, float* y, int ncol, cudaStream_t st) {
             KPM_CUDA(cudaEventRecord(ev[ev_used], st));
         }
         KPM_CUDA(cudaLaunchKernel(kernel, dim3(g1), dim3(RP_THREADS), args1, smem_bytes, st));
+        KPM_LAUNCHED();
+        KPM_CUDA(cudaLaunchKernel(kernel, dim3(g1), dim3(RP_THREADS), args2, smem_bytes, st));
         KPM_LAUNCHED();
         if (prof) {
             KPM_CUDA(cudaEventRecord(ev[ev_used + 1], st));
