@@ -17,11 +17,9 @@
 //
 // GEMM per tile: M = 128 columns J, K = KR (the row's nexc entries rounded up
 // to 16), N = P (NS + 1 rounded up to 16), operands in shared memory, D in
-// tensor memory (FP32).  x is split into two 16-bit pieces (FP16 with
-// power-of-two scales, or BF16) and W into three FP16 pieces where shared
-// memory allows (else two): MMAs A_hi B_j for every piece j plus A_lo B_0 keep
-// the integrals exact to 2^-33 (2^-22 with two pieces): H itself then carries
-// no rounding, and the vector's split rounds at 2^-22 per step.  The epilogue reads D
+// tensor memory (FP32).  Operands are split into two 16-bit pieces each (FP16
+// with power-of-two scales, or BF16), and three MMAs keep every product term
+// above 2^-22 relative: A_hi B_0, A_hi B_1, A_lo B_0.  The epilogue reads D
 // (tcgen05.ld) and scatters into the row's sigma in shared memory with 32-bit
 // fixed-point integer atomics (order-independent, so the result is
 // reproducible bit for bit).  One CTA per SM, persistent over rows; the kernel
@@ -714,22 +712,21 @@ size_t rowpass_smem(int P, int NW, int KR, int64_t Nc, int nst) {
 }
 
 template <int P>
-void* rowpass_fn(bool fp16, int nw) {
-    if (!fp16) return (void*)k_rowpass<P, false, 2>;
-    return nw == 3 ? (void*)k_rowpass<P, true, 3> : (void*)k_rowpass<P, true, 2>;
+void* rowpass_fn(bool fp16) {
+    return fp16 ? (void*)k_rowpass<P, true, 2> : (void*)k_rowpass<P, false, 2>;
 }
 
-void* rowpass_kernel(int P, bool fp16, int nw) {
+void* rowpass_kernel(int P, bool fp16) {
     switch (P) {
-        case 16: return rowpass_fn<16>(fp16, nw);
-        case 32: return rowpass_fn<32>(fp16, nw);
-        case 48: return rowpass_fn<48>(fp16, nw);
-        case 64: return rowpass_fn<64>(fp16, nw);
-        case 80: return rowpass_fn<80>(fp16, nw);
-        case 96: return rowpass_fn<96>(fp16, nw);
-        case 112: return rowpass_fn<112>(fp16, nw);
-        case 128: return rowpass_fn<128>(fp16, nw);
-        case 144: return rowpass_fn<144>(fp16, nw);
+        case 16: return rowpass_fn<16>(fp16);
+        case 32: return rowpass_fn<32>(fp16);
+        case 48: return rowpass_fn<48>(fp16);
+        case 64: return rowpass_fn<64>(fp16);
+        case 80: return rowpass_fn<80>(fp16);
+        case 96: return rowpass_fn<96>(fp16);
+        case 112: return rowpass_fn<112>(fp16);
+        case 128: return rowpass_fn<128>(fp16);
+        case 144: return rowpass_fn<144>(fp16);
         default: return nullptr;
     }
 }
@@ -748,8 +745,10 @@ void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
     nsb = B.ns;
     dim = nsa * nsb;
     fp16 = use_fp16;
+    nw = 2;
+    kernel = rowpass_kernel(P, fp16);
     KR = ((A.nexc + 15) / 16) * 16;
-    if (!rowpass_kernel(P, fp16, 2) || KR > RP_MAXK || A.ns > 32766 || B.ns > 32766)
+    if (!kernel || KR > RP_MAXK || A.ns > 32766 || B.ns > 32766)
         KPM_THROW(KPM_EUNSUPPORTED, "tensor-core sigma supports up to 16 orbitals");
     int dev = 0;
     KPM_CUDA(cudaGetDevice(&dev));
@@ -760,19 +759,14 @@ void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
     nsm = prop.multiProcessorCount;
     gbound = (float)(wcolsum * (1.0 + 1e-6));
     int64_t ncmax = nsa > nsb ? nsa : nsb;
-    // FP16: W in three pieces (every product term above 2^-33 of W, so the
-    // integrals carry no systematic rounding) with three A stages where both fit
-    // (10-14 orbitals); otherwise two pieces keep three stages (16 orbitals: the
-    // copies of a tile then have two MMA durations to land).  BF16: two pieces.
-    const size_t optin = (size_t)prop.sharedMemPerBlockOptin;
-    nw = (fp16 && rowpass_smem(P, 3, KR, ncmax, 3) <= optin) ? 3 : 2;
+    // three A stages where they fit (the copies of a tile then have two MMA
+    // durations to land), else two
     nst = 3;
     smem_bytes = rowpass_smem(P, nw, KR, ncmax, nst);
-    if (smem_bytes > optin) {
+    if (smem_bytes > (size_t)prop.sharedMemPerBlockOptin) {
         nst = 2;
         smem_bytes = rowpass_smem(P, nw, KR, ncmax, nst);
     }
-    kernel = rowpass_kernel(P, fp16, nw);
     // at least ~116 KB so that exactly one CTA (and one TMEM allocation) fits per SM
     size_t floor_bytes = 116 * 1024;
     if (smem_bytes < floor_bytes) smem_bytes = floor_bytes;

@@ -15,7 +15,7 @@ struct TcSigma {
     int64_t nsa = 0, nsb = 0, dim = 0;
     int nsm = 0;                  // SMs of the device (persistent grid)
     bool fp16 = false;            // operand format: split FP16 (scaled) or split BF16
-    int nw = 2;                   // 16-bit pieces of W (3 for FP16 where shared memory allows)
+    int nw = 2;                   // 16-bit pieces of W
     float wscale = 1.0f;          // power-of-two scale of W in the image
     float gbound = 0.0f;          // max over output slots of sum over input slots of |W|
     void* kernel = nullptr;       // k_rowpass instantiation for P
