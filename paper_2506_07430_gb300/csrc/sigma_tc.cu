@@ -151,7 +151,8 @@ struct RowPass {
     int KR;                  // K of the row GEMM: rnexc rounded up to 16
     const uint16_t* wrow;    // W by input slot: NW pieces of [P][P] 16-bit (bits of the format)
     uint32_t ncols;          // TMEM columns allocated
-    const float* amax;       // device max|x| (operand scaling and fixed-point range)
+    const float* amax;       // device max|x| (operand scaling)
+    const float* rowmax;     // [Nr] max |x| of each row (per-row fixed-point range)
     float wscale;            // power-of-two scale applied to W in the image
     float gbound;            // max over output slots of sum_k |W[k][s]| (unscaled W)
     int nexc_c;              // table entries per column string (contributions per target)
@@ -199,6 +200,12 @@ __device__ __forceinline__ Scales scales(float mx, bool fp16, float wscale, floa
     }
     c.bscale = c.fx / (c.sa * wscale);
     return c;
+}
+
+template <bool FP16>
+__device__ __forceinline__ float f16bits(uint16_t bits) {
+    if (FP16) return __half2float(__ushort_as_half(bits));
+    return __bfloat162float(__ushort_as_bfloat16(bits));
 }
 
 template <bool FP16>
@@ -285,9 +292,11 @@ __device__ __forceinline__ bool wait_phase(uint64_t* mbar, uint32_t parity, vola
 // Rows are separated by CTA barriers (set-up of the next row's B_R and sigma).
 //
 // Fixed-point range: integer addition wraps, so only each final row sum has to
-// fit in 32 bits, and it does whenever every term |D| < 2^31 / nexc_c.  The
-// first launch runs at a scale 2^shift finer than the a-priori bound that
-// guarantees this; the scatter warps track max |D| per row, and a row that
+// fit in 32 bits, and it does whenever every term |D| < 2^31 / nexc_c.  Per row
+// R, |D[J][s]| <= c_s = sum_e rowmax(tgt_e) |W[slot e][s]| (rowmax: max |x| of a
+// source row), which sets the row's a-priori scale (capped so that B_R stays in
+// range); vectors with small or empty source rows get a correspondingly finer
+// step.  The first launch runs at a scale 2^shift finer than that bound; the scatter warps track max |D| per row, and a row that
 // reaches the limit is not written but appended to a list that the second
 // launch (shift = 0, rows from the list) recomputes.  Which rows take the
 // second pass depends only on the data, so results stay reproducible.
@@ -306,7 +315,11 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
     int64_t* rowoff = reinterpret_cast<int64_t*>(
         (reinterpret_cast<uintptr_t>(srow + Nc + 1) + 15) & ~uintptr_t(15));  // [RP_MAXK]
     uint16_t* rsl = reinterpret_cast<uint16_t*>(rowoff + RP_MAXK);    // [RP_MAXK]
-    uintptr_t tail = (reinterpret_cast<uintptr_t>(rsl + RP_MAXK) + 15) & ~uintptr_t(15);
+    float* rmx = reinterpret_cast<float*>(
+        (reinterpret_cast<uintptr_t>(rsl + RP_MAXK) + 15) & ~uintptr_t(15));  // [RP_MAXK]
+    float* rsc = rmx + RP_MAXK;                                       // [4] row scales
+    unsigned* rred = reinterpret_cast<unsigned*>(rsc + 4);            // [2] row reductions
+    uintptr_t tail = (reinterpret_cast<uintptr_t>(rred + 2) + 15) & ~uintptr_t(15);
     uint64_t* afree = reinterpret_cast<uint64_t*>(tail);   // [3] stage s free (MMA done)
     uint64_t* afull = afree + 3;                           // [3] stage s copied
     uint64_t* dfull = afree + 6;                           // [2] D buffer d written
@@ -343,7 +356,6 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
     const uint32_t SBO_B = 16u * (uint32_t)KR;
     const int ntiles = (int)((Nc + 127) / 128);
     const Scales sc = scales(*p.amax, FP16, p.wscale, p.gbound, p.nexc_c, p.shift);
-    const float inv_fx = 1.f / sc.fx;
     // every target receives at most nexc_c terms: if each |D| (fixed-point units)
     // stays below this limit, every row sum fits in 32 bits
     const float dlimit = floorf(2147483648.f / (float)p.nexc_c) - 1.f;
@@ -367,14 +379,54 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
     for (int64_t idx = blockIdx.x; idx < nrows; idx += gridDim.x) {
         const int64_t ir = p.rows ? (int64_t)p.rows[idx] : idx;
         // ---- row set-up: zero sigma; the row's source rows, slots and signs; B_R
-        if (tid == 0) *range_flag = 0;
+        if (tid == 0) {
+            *range_flag = 0;
+            rred[0] = 0u;
+            rred[1] = 0u;
+        }
         for (int64_t j = tid; j <= Nc; j += RP_THREADS) srow[j] = 0;
         for (int e = tid; e < RP_MAXK; e += RP_THREADS) {
             const bool in = e < p.rnexc;
             rowoff[e] = in ? (int64_t)p.rtgt[ir * p.rnexc + e] * p.xpitch : -1;
             rsl[e] = in ? p.rslot[ir * p.rnexc + e] : (uint16_t)0xFFFFu;
+            rmx[e] = in ? p.rowmax[p.rtgt[ir * p.rnexc + e]] : 0.f;
         }
         __syncthreads();
+        // this row's fixed-point range: |D[J][s]| <= c_s = sum_e rowmax(tgt_e) |W[slot e][s]|
+        // (piece 0 of W is within 2^-8 of W in either format: 1 % margin)
+        if (tid < P) {
+            float c = 0.f, wm = 0.f;
+            for (int e = 0; e < p.rnexc; ++e) {
+                const float w = fabsf(f16bits<FP16>(__ldg(p.wrow + (size_t)(rsl[e] & 0x7FFFu) * P + tid)));
+                c = fmaf(rmx[e], w, c);
+                wm = fmaxf(wm, w);
+            }
+            atomicMax(rred, __float_as_uint(c));
+            atomicMax(rred + 1, __float_as_uint(wm));
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const float cmax = __uint_as_float(rred[0]) / p.wscale * 1.01f;
+            const float wmax = __uint_as_float(rred[1]) / p.wscale * 1.01f;
+            // each target receives at most nexc_c terms of magnitude <= cmax
+            const float bound = 1.02f * (float)p.nexc_c * cmax;
+            float fx = 1.f;
+            if (bound > 0.f && isfinite(bound)) {
+                int f;
+                frexpf(bound, &f);  // bound < 2^f
+                fx = ldexpf(1.f, 31 + p.shift - max(f, -90));
+                // B_R = W fx / sa stays below 2^15 in FP16
+                if (FP16 && wmax > 0.f) {
+                    const float lim = 30000.f * sc.sa / wmax;
+                    while (fx > lim) fx *= 0.5f;
+                }
+            }
+            rsc[0] = fx;
+            rsc[1] = fx / (sc.sa * p.wscale);
+            rsc[2] = 1.f / fx;
+        }
+        __syncthreads();
+        const float bscale_r = rsc[1];
 #pragma unroll 1
         for (int piece = 0; piece < NW; ++piece) {
             const uint16_t* wsrc = p.wrow + (size_t)piece * P * P;
@@ -384,7 +436,7 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
                 const uint16_t r = rsl[e];
                 uint16_t v = 0;
                 if (r != 0xFFFFu) {
-                    v = scale16<FP16>(__ldg(wsrc + (size_t)(r & 0x7FFFu) * P + nn), sc.bscale);
+                    v = scale16<FP16>(__ldg(wsrc + (size_t)(r & 0x7FFFu) * P + nn), bscale_r);
                     v ^= (uint16_t)(r & 0x8000u);   // exact negation
                 }
                 const uint32_t off = (uint32_t)(nn >> 3) * SBO_B + (uint32_t)(e >> 3) * 128u +
@@ -596,7 +648,7 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
             if (tid == 0) p.flagged[atomicAdd(p.nflagged, 1)] = (int)ir;
         } else {
             for (int64_t j = tid; j < Nc; j += RP_THREADS)
-                p.Y[ir * Nc + j] = (float)srow[j] * inv_fx;
+                p.Y[ir * Nc + j] = (float)srow[j] * rsc[2];
         }
         __syncthreads();
     }
@@ -605,15 +657,27 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
     if (warp == 0) tmem_dealloc(tbase, p.ncols);
 }
 
-// max |x| as float bits (non-negative floats order like unsigned integers)
-__global__ void k_absmax(const float* __restrict__ x, int64_t n, unsigned* out) {
-    float mx = 0.f;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        mx = fmaxf(mx, fabsf(x[i]));
-    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(mx));
+// max |x| of each row (rowmax[r]) and of all rows (out, float bits: non-negative
+// floats order like unsigned integers)
+__global__ void k_rowmax(const float* __restrict__ x, int64_t nrow, int64_t ncol,
+                         float* __restrict__ rowmax, unsigned* out) {
+    __shared__ float wmx[8];
+    for (int64_t r = blockIdx.x; r < nrow; r += gridDim.x) {
+        float mx = 0.f;
+        for (int64_t j = threadIdx.x; j < ncol; j += blockDim.x) mx = fmaxf(mx, fabsf(x[r * ncol + j]));
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        if ((threadIdx.x & 31) == 0) wmx[threadIdx.x >> 5] = mx;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float m = wmx[0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, wmx[w]);
+            rowmax[r] = m;
+            atomicMax(out, __float_as_uint(m));
+        }
+        __syncthreads();
+    }
 }
+
 
 // ---------------------------------------------------------------- set-up kernels
 
@@ -708,7 +772,7 @@ uint32_t tmem_cols(int P) {
 
 size_t rowpass_smem(int P, int NW, int KR, int64_t Nc, int nst) {
     return (size_t)2 * nst * KR * 256 + (size_t)2 * NW * P * KR + 4 * (size_t)(Nc + 1) + 16 +
-           10 * RP_MAXK + 16 + 10 * 8 + 16;
+           10 * RP_MAXK + 16 + 4 * RP_MAXK + 24 + 16 + 10 * 8 + 16;
 }
 
 template <int P>
@@ -832,7 +896,12 @@ void TcSigma::apply(const float* x, float* y, int ncol, cudaStream_t st) {
         float* Y = y + (size_t)c * dim;
         // max|x|: FP16 operand scales and the fixed-point range of the scatter
         KPM_CUDA(cudaMemsetAsync(amax.p, 0, sizeof(unsigned), st));
-        k_absmax<<<1024, 256, 0, st>>>(X, dim, amax.as<unsigned>());
+        rowmax.ensure((size_t)(nsa > 0 ? nsa : 1) * sizeof(float));
+        {
+            const int64_t g = nsa < (int64_t)nsm * 8 ? nsa : (int64_t)nsm * 8;
+            k_rowmax<<<(unsigned)(g > 0 ? g : 1), 256, 0, st>>>(X, nsa, nsb, rowmax.as<float>(),
+                                                                amax.as<unsigned>());
+        }
         KPM_LAUNCHED();
         const float* am = reinterpret_cast<const float*>(amax.p);
         // split x: the FP16 pieces serve the row pass and the beta GEMM
@@ -855,7 +924,8 @@ void TcSigma::apply(const float* x, float* y, int ncol, cudaStream_t st) {
         KPM_CUDA(cudaMemsetAsync(nflag.p, 0, sizeof(int), st));
         RowPass p1{xh, xl, xp, Y, nsa, nsb, slot_b.as<uint4>(),
                    ta->tgt.as<int32_t>(), rslot_a.as<uint16_t>(), ta->nexc, KR,
-                   wimg.as<uint16_t>(), nc, am, wscale, gbound, tb->nexc, NS, nst, RP_SHIFT,
+                   wimg.as<uint16_t>(), nc, am, rowmax.as<float>(), wscale, gbound, tb->nexc, NS,
+                   nst, RP_SHIFT,
                    nullptr, nullptr, flagged.as<int>(), nflag.as<int>(), err.as<int>()};
         RowPass p2 = p1;
         p2.shift = 0;

@@ -28,6 +28,7 @@ struct TcSigma {
     DenseSS dense;                // same-spin parts (dense GEMMs with F_a, F_b)
     DevBuf err;                   // int error flag (1: a bounded wait ran out)
     DevBuf amax;                  // max |x| (float bits): operand scale, fixed-point range
+    DevBuf rowmax;                // [N_a] max |x| per row: per-row fixed-point range of the row pass
     DevBuf flagged, nflag;        // rows redone at the a-priori fixed-point scale, and their count
     int nst = 2;                  // A stages of the row pass (3 where shared memory allows)
     size_t smem_bytes = 0;
