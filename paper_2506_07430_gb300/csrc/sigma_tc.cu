@@ -172,10 +172,11 @@ constexpr int RP_MMA_WARP = RP_SCATTER_WARPS + RP_COPY_WARPS;   // MMA issue (on
 constexpr int RP_WARPS = RP_SCATTER_WARPS + RP_COPY_WARPS + 1;
 constexpr int RP_THREADS = 32 * RP_WARPS;
 constexpr int RP_MAXK = 96;                  // largest KR: 9 * 10 = 90 entries rounded up
-// first-pass fixed-point scale: 2^RP_SHIFT times the a-priori one (the terms of a
-// vector are normally far below the a-priori per-term bound; rows whose terms
+// first-pass fixed-point scale: 2^RP_SHIFT times the per-row a-priori one (the
+// largest term of a dense vector's row is typically ~1/7 of that row's per-term
+// bound, so a factor 4 leaves margin and rows are rarely redone; rows whose terms
 // come within the 32-bit headroom are redone at the a-priori scale)
-constexpr int RP_SHIFT = 3;
+constexpr int RP_SHIFT = 2;
 constexpr uint32_t A_LBO = 2048;             // A stage: K-group (8 entries) stride, bytes
 constexpr uint32_t A_SBO = 128;              // A stage: MN-group (8 columns) stride, bytes
 
