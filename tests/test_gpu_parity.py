@@ -4,7 +4,7 @@ Tolerances:
 * string tables: bit-exact;
 * FP64 sigma: |dy| <= 1e-12 * max|y| (FP64 rounding of sums of ~1e3-1e4 terms);
 * FP32 sigma: |dy| <= 2e-6 * max|y| (FP32 unit roundoff 6e-8 times the growth of
-  sums of ~1e3 terms, stated in DESIGN.md);
+  sums of ~1e3 terms, with headroom);
 * moments: FP64 <= 1e-10 Omega_0.  For paths with FP32 vectors the error grows
   linearly with the moment index (a systematic eigenvalue shift dE moves
   Omega_n by ~ n dE / a): bound 4 N u Omega_0 with u the relative error per
