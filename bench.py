@@ -364,6 +364,7 @@ def run_ours(args, ws, rank, local, pg):
                 "d2h_bytes_per_step": nm_e2e * 8,
                 "note": f"kpm_moments_host, {nm_e2e} moments per request, psi0 from pinned host memory"},
         "gpu_launches": int(launches),
+        "tuned": dict(zip(("gemm_group_beta", "gemm_group_alpha"), k.tuned_params())),
         "clocks": clk,
         "moments_ok": moments_ok,
     }

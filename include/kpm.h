@@ -212,6 +212,16 @@ kpm_status kpm_spectrum(const double* moments, int nmoments, double a, double b,
 kpm_status kpm_synchronize(kpm_ctx* ctx);
 
 /*
+ * kpm_tuned_params -- the launch choices the library's autotuner made for this
+ * context at creation: the rasterisation group (row tiles that sweep the column
+ * tiles together, for L2 reuse) of the beta and alpha same-spin GEMMs of the
+ * tensor-core paths, picked from {4, 8, 16, 32} by timing each once per device
+ * and shape (16 for shapes too small to tune).  The choice never changes
+ * results.  FP64 / FP32 contexts report 0.  Errors: KPM_EINVAL for NULL ctx.
+ */
+kpm_status kpm_tuned_params(const kpm_ctx* ctx, int* group_beta, int* group_alpha);
+
+/*
  * kpm_graphs_enable -- kpm_recursion_advance (and kpm_moments, the server)
  * issue pairs of Chebyshev steps as replays of CUDA graphs captured on first
  * use (one per assignment of the two rotating recursion vectors; the step

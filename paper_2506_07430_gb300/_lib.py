@@ -42,6 +42,7 @@ SIGNATURES = {
     "kpm_profile_read": (_I, [_P, _P, _P]),
     "kpm_profile_read_rowpass": (_I, [_P, _P, _P]),
     "kpm_graphs_enable": (_I, [_P, _I]),
+    "kpm_tuned_params": (_I, [_P, _P, _P]),
     "kpm_spectrum_static": (_I, [_P, _I, _D, _D, _I, _I, _P, _P, _P]),
     "kpm_server_create": (_I, [_P, _P]),
     "kpm_server_submit": (_I, [_P, _P, _P]),
@@ -239,6 +240,12 @@ class KPM:
 
     def synchronize(self):
         _check(self._lib().kpm_synchronize(self._h), self._h)
+
+    def tuned_params(self):
+        """Autotuner choices: (rasterisation group of the beta GEMM, of the alpha GEMM)."""
+        gb, ga = ctypes.c_int(), ctypes.c_int()
+        _check(self._lib().kpm_tuned_params(self._h, ctypes.byref(gb), ctypes.byref(ga)), self._h)
+        return gb.value, ga.value
 
     def graphs_enable(self, on: bool = True):
         _check(self._lib().kpm_graphs_enable(self._h, 1 if on else 0), self._h)

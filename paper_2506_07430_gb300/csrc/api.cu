@@ -623,6 +623,13 @@ kpm_status kpm_profile_read_rowpass(kpm_ctx* ctx, double* ms, int* count) {
     });
 }
 
+kpm_status kpm_tuned_params(const kpm_ctx* ctx, int* group_beta, int* group_alpha) {
+    if (!ctx) { g_err = "NULL context"; return KPM_EINVAL; }
+    if (group_beta) *group_beta = ctx->tc ? ctx->tc->dense.group_m[0] : 0;
+    if (group_alpha) *group_alpha = ctx->tc ? ctx->tc->dense.group_m[1] : 0;
+    return KPM_OK;
+}
+
 kpm_status kpm_graphs_enable(kpm_ctx* ctx, int enable) {
     if (!ctx) { g_err = "NULL context"; return KPM_EINVAL; }
     ctx->graphs = enable != 0;

@@ -28,6 +28,8 @@
 
 #include <cmath>
 #include <cstring>
+#include <array>
+#include <map>
 #include <mutex>
 
 #include "gemm_tc.cuh"
@@ -145,6 +147,7 @@ struct GemmArgs {
     const float2* dm;
     const float2* dn;
     int* err;
+    int group_m;               // row tiles per rasterisation group (tuned; see DenseSS::autotune)
 };
 
 // bounded wait that also gives up when another role has aborted
@@ -191,7 +194,7 @@ k_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensor
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // grouped rasterisation: groups of GROUP_M row tiles walk all column tiles,
     // so the group's A panels and the current B panels stay in L2
-    constexpr int GROUP_M = 16;
+    const int GROUP_M = g.group_m;
     const int nM = (g.M + GM_BM - 1) / GM_BM, nN = (g.N + GM_BN - 1) / GM_BN;
     const int b = blockIdx.x;
     const int gsize = GROUP_M * nN;
@@ -566,6 +569,33 @@ void DenseSS::split(const float* x, const float* amax, cudaStream_t st) {
     KPM_LAUNCHED();
 }
 
+// beta: out[m = I_b][n = I_a] = sum_J Fb[I_b][J] x[I_a][J]   (x rows from split())
+void DenseSS::launch_beta(float* y, const float* amax, int group, cudaStream_t st) {
+    CUtensorMap a0 = make_map(fb_hi.as<__half>(), nb, nb, pb, GM_BM);
+    CUtensorMap a1 = make_map(fb_lo.as<__half>(), nb, nb, pb, GM_BM);
+    CUtensorMap b0 = make_map(xh.as<__half>(), na, nb, xpitch, GM_BN);
+    CUtensorMap b1 = make_map(xl.as<__half>(), na, nb, xpitch, GM_BN);
+    GemmArgs g{(int)nb, (int)na, (int)nb, y, nb, 1.0f, amax, (float)wscale_b,
+               nullptr, nullptr, nullptr, err, group};
+    dim3 grid((unsigned)(((nb + GM_BM - 1) / GM_BM) * ((na + GM_BN - 1) / GM_BN)));
+    k_gemm<<<grid, GM_THREADS, smem, st>>>(a0, a1, b0, b1, g);
+    KPM_LAUNCHED();
+}
+
+// alpha: out[m = I_b][n = I_a] = sum_J x^T[I_b][J] Fa[I_a][J], plus the exact diagonals
+void DenseSS::launch_alpha(const float* x, float* y, const float* amax, int group,
+                           cudaStream_t st) {
+    CUtensorMap a0 = make_map(th.as<__half>(), nb, na, pa, GM_BM);
+    CUtensorMap a1 = make_map(tl.as<__half>(), nb, na, pa, GM_BM);
+    CUtensorMap b0 = make_map(fa_hi->as<__half>(), na, na, pa, GM_BN);
+    CUtensorMap b1 = make_map(fa_lo->as<__half>(), na, na, pa, GM_BN);
+    GemmArgs g{(int)nb, (int)na, (int)na, y, nb, 1.0f, amax, (float)wscale_a,
+               x, db.as<float2>(), da->as<float2>(), err, group};
+    dim3 grid((unsigned)(((nb + GM_BM - 1) / GM_BM) * ((na + GM_BN - 1) / GM_BN)));
+    k_gemm<<<grid, GM_THREADS, smem, st>>>(a0, a1, b0, b1, g);
+    KPM_LAUNCHED();
+}
+
 void DenseSS::apply(const float* x, float* y, const float* amax, cudaStream_t st) {
     // transposed split copy of x (cols beta x rows alpha); the row split is xh/xl
     th.ensure((size_t)nb * pa * 2);
@@ -573,30 +603,74 @@ void DenseSS::apply(const float* x, float* y, const float* amax, cudaStream_t st
     dim3 tb(32, 8), gt((unsigned)((nb + 31) / 32), (unsigned)((na + 31) / 32));
     k_split_transpose<<<gt, tb, 0, st>>>(x, na, nb, th.as<__half>(), tl.as<__half>(), pa, amax);
     KPM_LAUNCHED();
-    // beta: out[m = I_b][n = I_a] = sum_J Fb[I_b][J] x[I_a][J]
+    launch_beta(y, amax, group_m[0], st);
+    launch_alpha(x, y, amax, group_m[1], st);
+}
+
+// Picks the rasterisation group of each GEMM by timing the candidates once per
+// device and shape (process-wide cache).  The group only decides which CTA
+// computes which output tile, never how a tile is computed, so results do not
+// depend on the choice.  Small shapes, where the whole problem sits in L2, keep
+// the default.
+void DenseSS::autotune(cudaStream_t st) {
+    if (na * nb < ((int64_t)1 << 22)) return;
+    int dev = 0;
+    KPM_CUDA(cudaGetDevice(&dev));
+    static std::mutex mu;
+    static std::map<std::array<int64_t, 3>, std::array<int, 2>> cache;
+    const std::array<int64_t, 3> key{dev, na, nb};
     {
-        CUtensorMap a0 = make_map(fb_hi.as<__half>(), nb, nb, pb, GM_BM);
-        CUtensorMap a1 = make_map(fb_lo.as<__half>(), nb, nb, pb, GM_BM);
-        CUtensorMap b0 = make_map(xh.as<__half>(), na, nb, xpitch, GM_BN);
-        CUtensorMap b1 = make_map(xl.as<__half>(), na, nb, xpitch, GM_BN);
-        GemmArgs g{(int)nb, (int)na, (int)nb, y, nb, 1.0f, amax, (float)wscale_b,
-                   nullptr, nullptr, nullptr, err};
-        dim3 grid((unsigned)(((nb + GM_BM - 1) / GM_BM) * ((na + GM_BN - 1) / GM_BN)));
-        k_gemm<<<grid, GM_THREADS, smem, st>>>(a0, a1, b0, b1, g);
-        KPM_LAUNCHED();
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            group_m[0] = it->second[0];
+            group_m[1] = it->second[1];
+            return;
+        }
     }
-    // alpha: out[m = I_b][n = I_a] = sum_J x^T[I_b][J] Fa[I_a][J], plus the exact diagonals
-    {
-        CUtensorMap a0 = make_map(th.as<__half>(), nb, na, pa, GM_BM);
-        CUtensorMap a1 = make_map(tl.as<__half>(), nb, na, pa, GM_BM);
-        CUtensorMap b0 = make_map(fa_hi->as<__half>(), na, na, pa, GM_BN);
-        CUtensorMap b1 = make_map(fa_lo->as<__half>(), na, na, pa, GM_BN);
-        GemmArgs g{(int)nb, (int)na, (int)na, y, nb, 1.0f, amax, (float)wscale_a,
-                   x, db.as<float2>(), da->as<float2>(), err};
-        dim3 grid((unsigned)(((nb + GM_BM - 1) / GM_BM) * ((na + GM_BN - 1) / GM_BN)));
-        k_gemm<<<grid, GM_THREADS, smem, st>>>(a0, a1, b0, b1, g);
-        KPM_LAUNCHED();
+    // scratch operands (zeros: the timing does not depend on the values)
+    xh.ensure((size_t)na * xpitch * 2);
+    xl.ensure((size_t)na * xpitch * 2);
+    th.ensure((size_t)nb * pa * 2);
+    tl.ensure((size_t)nb * pa * 2);
+    KPM_CUDA(cudaMemsetAsync(xh.p, 0, xh.bytes, st));
+    KPM_CUDA(cudaMemsetAsync(xl.p, 0, xl.bytes, st));
+    KPM_CUDA(cudaMemsetAsync(th.p, 0, th.bytes, st));
+    KPM_CUDA(cudaMemsetAsync(tl.p, 0, tl.bytes, st));
+    DevBuf ys, one;
+    ys.alloc((size_t)na * nb * sizeof(float));
+    KPM_CUDA(cudaMemsetAsync(ys.p, 0, ys.bytes, st));
+    static const float kOne = 1.0f;
+    one.alloc(sizeof(float));
+    KPM_CUDA(cudaMemcpyAsync(one.p, &kOne, sizeof(float), cudaMemcpyHostToDevice, st));
+    cudaEvent_t e0, e1;
+    KPM_CUDA(cudaEventCreate(&e0));
+    KPM_CUDA(cudaEventCreate(&e1));
+    const int cand[4] = {4, 8, 16, 32};
+    for (int which = 0; which < 2; ++which) {
+        auto run = [&](int gsz) {
+            if (which == 0) launch_beta(ys.as<float>(), one.as<float>(), gsz, st);
+            else launch_alpha(ys.as<float>(), ys.as<float>(), one.as<float>(), gsz, st);
+        };
+        run(group_m[which]);  // warm-up
+        float best = 0.f;
+        for (int c : cand) {
+            KPM_CUDA(cudaEventRecord(e0, st));
+            run(c);
+            KPM_CUDA(cudaEventRecord(e1, st));
+            KPM_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            KPM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (best == 0.f || ms < best) {
+                best = ms;
+                group_m[which] = c;
+            }
+        }
     }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = {group_m[0], group_m[1]};
 }
 
 }  // namespace kpm

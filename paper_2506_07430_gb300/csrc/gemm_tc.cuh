@@ -30,6 +30,12 @@ struct DenseSS {
     // y += (F_a (x) 1 + 1 (x) F_b) x, the diagonals exactly; amax = device max|x|.
     // Uses xh/xl from split(x) on the same stream.
     void apply(const float* x, float* y, const float* amax, cudaStream_t st);
+    // Rasterisation group (row tiles per group) of the beta and alpha GEMMs, chosen
+    // by autotune() at set-up; 16 by default.
+    int group_m[2] = {16, 16};
+    void autotune(cudaStream_t st);
+    void launch_beta(float* y, const float* amax, int group, cudaStream_t st);
+    void launch_alpha(const float* x, float* y, const float* amax, int group, cudaStream_t st);
 };
 
 }  // namespace kpm

@@ -887,6 +887,7 @@ void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
     nflag.alloc(sizeof(int));
     KPM_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
     dense.init(A, B, &A == &B, err.as<int>(), st);
+    dense.autotune(st);
 }
 
 void TcSigma::apply(const float* x, float* y, int ncol, cudaStream_t st) {

@@ -448,3 +448,21 @@ def test_graph_steps_equal_direct_steps(torch, prec, n, ne):
         k.close()
     assert out[0].shape == (2, 80)
     assert np.array_equal(out[0], out[1])
+
+
+def test_autotuned_gemm_groups(torch):
+    """The autotuner's rasterisation choices are among its candidates (14 orbitals
+    and up are tuned, smaller shapes keep 16), and tuning leaves results alone:
+    the tuned context's sigma matches the oracle on sampled rows like any other."""
+    I = synthetic.integrals(8, 4, 4, 2506071)
+    k = _kpm(I, 8, 4, 4, "mixed")
+    assert k.tuned_params() == (16, 16)
+    k.close()
+    k = _kpm(I, 8, 4, 4, "fp64")
+    assert k.tuned_params() == (0, 0)
+    k.close()
+    I = synthetic.integrals(14, 7, 7, 2506074)
+    k = _kpm(I, 14, 7, 7, "mixed")
+    gb, ga = k.tuned_params()
+    assert gb in (4, 8, 16, 32) and ga in (4, 8, 16, 32)
+    k.close()
