@@ -43,6 +43,10 @@ constexpr int GM_TMA_WARP = GM_EPI_WARPS;       // producer (one thread)
 constexpr int GM_MMA_WARP = GM_EPI_WARPS + 1;   // MMA issue (one thread)
 constexpr int GM_THREADS = 32 * (GM_EPI_WARPS + 2);
 constexpr int GM_CHUNKS = 24;                   // target number of accumulation chunks over K
+// poll interval of the epilogue warps' waits (a chunk accumulates for microseconds)
+#ifndef GM_BACKOFF_NS
+#define GM_BACKOFF_NS 256
+#endif
 constexpr uint32_t A_BYTES = GM_BM * GM_BK * 2;  // 16 KB per piece
 constexpr uint32_t B_BYTES = GM_BN * GM_BK * 2;  // 32 KB per piece
 constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
@@ -150,11 +154,14 @@ struct GemmArgs {
     int group_m;               // row tiles per rasterisation group (tuned; see DenseSS::autotune)
 };
 
-// bounded wait that also gives up when another role has aborted
+// bounded wait that also gives up when another role has aborted; roles off the
+// critical path sleep backoff_ns between polls so that they leave the issue
+// slots to the MMA and TMA threads
 __device__ __forceinline__ bool wait_or_abort(uint64_t* b, uint32_t parity, volatile int* abort_flag,
-                                              int* err) {
+                                              int* err, unsigned backoff_ns = 0) {
     long long t0 = clock64();
     while (!mbar_test(b, parity)) {
+        if (backoff_ns) __nanosleep(backoff_ns);
         if (*abort_flag) return false;
         if (clock64() - t0 > GM_WAIT) {
             *abort_flag = 1;
@@ -297,7 +304,8 @@ k_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensor
         for (int u = 0; u < 128; ++u) rs[u] = 0.f;
         bool ok = true;
         for (int c = 0; c < nchunk && ok; ++c) {
-            if (lane == 0) ok = wait_or_abort(&accf[c & 1], (c >> 1) & 1, abort_flag, g.err);
+            if (lane == 0)
+                ok = wait_or_abort(&accf[c & 1], (c >> 1) & 1, abort_flag, g.err, GM_BACKOFF_NS);
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok) break;
             tc_after();

@@ -144,7 +144,7 @@ struct RowPass {
     int64_t Nr, Nc;
     const uint4* tslot8;     // [P/8][Nc]: 8 16-bit entries per chunk of 8 slots (slot 8c+u in
                              // half u of the 128-bit word): target string | sign << 15,
-                             // Nc when the slot is absent
+                             // Nc + (J mod 32) when the slot of column J is absent
     const int32_t* rtgt;     // [Nr][rnexc] row-string targets
     const uint16_t* rslot;   // [Nr][rnexc] row-string slot | sign << 15
     int rnexc;               // table entries per row string
@@ -172,11 +172,20 @@ constexpr int RP_MMA_WARP = RP_SCATTER_WARPS + RP_COPY_WARPS;   // MMA issue (on
 constexpr int RP_WARPS = RP_SCATTER_WARPS + RP_COPY_WARPS + 1;
 constexpr int RP_THREADS = 32 * RP_WARPS;
 constexpr int RP_MAXK = 96;                  // largest KR: 9 * 10 = 90 entries rounded up
+// sink cells after the row's sigma: an absent slot of column J targets cell
+// Nc + (J mod 32), so the scatter adds every slot without a branch and the 32
+// lanes of a warp (32 consecutive J) sink into 32 different banks
+constexpr int RP_SINK = 32;
 // first-pass fixed-point scale: 2^RP_SHIFT times the per-row a-priori one (the
 // largest term of a dense vector's row is typically ~1/7 of that row's per-term
 // bound, so a factor 4 leaves margin and rows are rarely redone; rows whose terms
 // come within the 32-bit headroom are redone at the a-priori scale)
 constexpr int RP_SHIFT = 2;
+// poll interval of the copy and MMA warps' waits (the MMA of tile t + 1 has
+// about one scatter duration of slack, microseconds)
+#ifndef RP_BACKOFF_NS
+#define RP_BACKOFF_NS 256
+#endif
 constexpr uint32_t A_LBO = 2048;             // A stage: K-group (8 entries) stride, bytes
 constexpr uint32_t A_SBO = 128;              // A stage: MN-group (8 columns) stride, bytes
 
@@ -244,13 +253,16 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* mbar, uint32_t par
     return ok != 0;
 }
 
-// Bounded wait on an mbarrier phase (the waiting thread is suspended, not
-// spinning); false (and the CTA's abort flag set) when the wait ran out or
-// another role has aborted.
+// Bounded wait on an mbarrier phase; false (and the CTA's abort flag set) when
+// the wait ran out or another role has aborted.  try_wait's suspension ends
+// long before its time hint (tens of cycles), so a waiting warp would still
+// take a large share of its sub-partition's issue slots from the scatter warps;
+// roles off the critical path sleep backoff_ns between polls.
 __device__ __forceinline__ bool wait_phase(uint64_t* mbar, uint32_t parity, volatile int* abort_flag,
-                                           int* err) {
+                                           int* err, unsigned backoff_ns = 0) {
     const long long t0 = clock64();
     while (!mbar_try_wait_sleep(mbar, parity)) {
+        if (backoff_ns) __nanosleep(backoff_ns);
         if (*abort_flag) return false;
         if (clock64() - t0 > WAIT_CYCLES) {
             *abort_flag = 1;
@@ -276,8 +288,8 @@ __device__ __forceinline__ bool wait_phase(uint64_t* mbar, uint32_t parity, vola
 // (canonical K-major layout without swizzle).  MMA passes: A_hi B_j for every
 // piece j of W, plus A_lo B_0; D accumulates in tensor memory, two buffers deep.
 //
-// Warp roles, synchronised per tile by mbarriers only (waiting threads are
-// suspended on the barrier, so they take no issue slots from the others):
+// Warp roles, synchronised per tile by mbarriers only (the copy and MMA warps
+// poll theirs with a sleep in between, leaving the issue slots to the scatter):
 //   copy (warps 16-18, a third of the copies each): copies of tile t into
 //     stage t % nst once MMA(t - nst) has released it; once they have landed
 //     (and been fenced for the async proxy), each arrives on "A full";
@@ -312,9 +324,9 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
     uint8_t* sA = smem;                                               // [nst stages][2 pieces]
     uint8_t* sB = smem + 2 * nst * a_piece;                           // NW pieces of P x KR
     const uint32_t b_piece = (uint32_t)(P * KR * 2);
-    int* srow = reinterpret_cast<int*>(sB + NW * b_piece);            // Nc + 1, fixed point
+    int* srow = reinterpret_cast<int*>(sB + NW * b_piece);            // Nc + RP_SINK, fixed point
     int64_t* rowoff = reinterpret_cast<int64_t*>(
-        (reinterpret_cast<uintptr_t>(srow + Nc + 1) + 15) & ~uintptr_t(15));  // [RP_MAXK]
+        (reinterpret_cast<uintptr_t>(srow + Nc + RP_SINK) + 15) & ~uintptr_t(15));  // [RP_MAXK]
     uint16_t* rsl = reinterpret_cast<uint16_t*>(rowoff + RP_MAXK);    // [RP_MAXK]
     float* rmx = reinterpret_cast<float*>(
         (reinterpret_cast<uintptr_t>(rsl + RP_MAXK) + 15) & ~uintptr_t(15));  // [RP_MAXK]
@@ -361,7 +373,6 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
     // stays below this limit, every row sum fits in 32 bits
     const float dlimit = floorf(2147483648.f / (float)p.nexc_c) - 1.f;
     const int64_t nrows = p.rows ? (int64_t)*p.nrows : p.Nr;
-    const uint32_t absent = (uint32_t)Nc;
 
     // scatter geometry (warps 0-15): used chunks of 8 slots, full chunks per
     // warp, and the remainder shared out two slots at a time
@@ -385,7 +396,7 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
             rred[0] = 0u;
             rred[1] = 0u;
         }
-        for (int64_t j = tid; j <= Nc; j += RP_THREADS) srow[j] = 0;
+        for (int64_t j = tid; j < Nc + RP_SINK; j += RP_THREADS) srow[j] = 0;
         for (int e = tid; e < RP_MAXK; e += RP_THREADS) {
             const bool in = e < p.rnexc;
             rowoff[e] = in ? (int64_t)p.rtgt[ir * p.rnexc + e] * p.xpitch : -1;
@@ -506,7 +517,8 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
                 if (gt >= nst) {
                     // stage gt % nst is free once MMA(gt - nst) has completed
                     if (lane == 0)
-                        ok = wait_phase(afree + gt % nst, (gt / nst - 1) & 1u, abort_flag, p.err);
+                        ok = wait_phase(afree + gt % nst, (gt / nst - 1) & 1u, abort_flag, p.err,
+                                        RP_BACKOFF_NS);
                     ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
                     if (!ok) break;
                 }
@@ -525,9 +537,10 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
                     const uint32_t sg = gi % nst;
                     const uint32_t st = sA_addr + sg * 2u * a_piece;
                     const uint32_t d = tbase + (gi & 1u) * (uint32_t)P;
-                    if (!wait_phase(afull + sg, (gi / nst) & 1u, abort_flag, p.err)) break;
+                    if (!wait_phase(afull + sg, (gi / nst) & 1u, abort_flag, p.err, RP_BACKOFF_NS))
+                        break;
                     if (gi >= 2 && !wait_phase(dfree + (gi & 1u), ((gi >> 1) - 1) & 1u,
-                                               abort_flag, p.err))
+                                               abort_flag, p.err, RP_BACKOFF_NS))
                         break;
                     tc_fence_after();
                     // descriptor address fields advance by (bytes >> 4): K step = 2 K-groups
@@ -555,14 +568,20 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
         } else {
             // ---- scatter
             uint32_t w[MAXF][4], wt[3];
+            // columns past Nc (the ragged last tile) sink every slot: cell Nc + lane
+            // (the tile starts at a multiple of 128, so J mod 32 = lane)
+            const uint32_t sink = (uint32_t)Nc + (uint32_t)lane;
+            const uint32_t sink2 = sink | (sink << 16);
             auto load_words = [&](int t) {
                 const int64_t jc = (int64_t)t * 128 + m;
-                const int64_t jcc = jc < Nc ? jc : Nc - 1;
+                const bool in = jc < Nc;
+                const int64_t jcc = in ? jc : Nc - 1;
 #pragma unroll
                 for (int k = 0; k < MAXF; ++k) {
                     if (k < nfull) {
                         const uint4 v = __ldg(p.tslot8 + (int64_t)(wq + 4 * k) * Nc + jcc);
-                        w[k][0] = v.x; w[k][1] = v.y; w[k][2] = v.z; w[k][3] = v.w;
+                        w[k][0] = in ? v.x : sink2; w[k][1] = in ? v.y : sink2;
+                        w[k][2] = in ? v.z : sink2; w[k][3] = in ? v.w : sink2;
                     }
                 }
 #pragma unroll
@@ -571,18 +590,20 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
                         const int s0 = tail0 + 2 * i;      // even: a pair within one chunk
                         const uint32_t* q = reinterpret_cast<const uint32_t*>(
                             p.tslot8 + (int64_t)(s0 >> 3) * Nc + jcc);
-                        wt[i] = __ldg(q + ((s0 & 7) >> 1));
+                        const uint32_t v = __ldg(q + ((s0 & 7) >> 1));
+                        wt[i] = in ? v : sink2;
                     }
                 }
             };
-            // one present slot: sigma[tgt] += sign * round(D); tg == Nc marks an absent slot
+            // one slot: sigma[tgt] += sign * round(D), unconditionally (an absent
+            // slot's target is this lane's sink cell)
             float dmax = 0.f;    // largest |D| this thread has seen in the row
-            auto add = [&](uint32_t word, int half, uint32_t dbits, bool valid) {
+            auto add = [&](uint32_t word, int half, uint32_t dbits) {
                 const uint32_t tg = half ? (word >> 16) & 0x7FFFu : word & 0x7FFFu;
                 const uint32_t sg = half ? (word & 0x80000000u) : (word << 16) & 0x80000000u;
                 dmax = fmaxf(dmax, fabsf(__uint_as_float(dbits)));
                 const int q = __float2int_rn(__uint_as_float(dbits ^ sg));
-                if (valid && tg != absent) atomicAdd(srow + tg, q);
+                atomicAdd(srow + tg, q);
             };
             bool ok = true;
             if (ntiles > 0) load_words(0);
@@ -622,19 +643,18 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
 #pragma unroll
                 for (int i = 0; i < 3; ++i) ct[i] = wt[i];
                 if (t + 1 < ntiles) load_words(t + 1);
-                const bool valid = (int64_t)t * 128 + m < Nc;
 #pragma unroll
                 for (int k = 0; k < MAXF; ++k) {
                     if (k < nfull) {
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) add(cw[k][u >> 1], u & 1, dr[k][u], valid);
+                        for (int u = 0; u < 8; ++u) add(cw[k][u >> 1], u & 1, dr[k][u]);
                     }
                 }
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
                     if (i < rem) {
-                        add(ct[i], 0, dt[2 * i], valid);
-                        add(ct[i], 1, dt[2 * i + 1], valid);
+                        add(ct[i], 0, dt[2 * i]);
+                        add(ct[i], 1, dt[2 * i + 1]);
                     }
                 }
             }
@@ -718,13 +738,13 @@ __global__ void k_wimg(const double* __restrict__ eri, int n, int P, int NS, int
 }
 
 // slot table: for string j and its entry (pq -> tgt, sgn), slot s = {p,q} holds
-// tgt | (sgn < 0) << 15; slots without an entry hold ns.  Stored per chunk of 8
-// slots: the 128-bit word (s/8, j) holds slots 8*(s/8) .. 8*(s/8)+7, slot s in
-// 16-bit half s%8.
-__global__ void k_slot_fill(uint16_t* __restrict__ tslot, int64_t count, uint16_t v) {
+// tgt | (sgn < 0) << 15; slots without an entry hold the sink ns + (j mod 32).
+// Stored per chunk of 8 slots: the 128-bit word (s/8, j) holds slots
+// 8*(s/8) .. 8*(s/8)+7, slot s in 16-bit half s%8.
+__global__ void k_slot_fill(uint16_t* __restrict__ tslot, int64_t count, int64_t ns) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
          i += (int64_t)gridDim.x * blockDim.x)
-        tslot[i] = v;
+        tslot[i] = (uint16_t)(ns + ((i >> 3) % ns & 31));
 }
 
 __global__ void k_slot_table(const int32_t* __restrict__ tgt, const uint16_t* __restrict__ pq,
@@ -772,7 +792,7 @@ uint32_t tmem_cols(int P) {
 }
 
 size_t rowpass_smem(int P, int NW, int KR, int64_t Nc, int nst) {
-    return (size_t)2 * nst * KR * 256 + (size_t)2 * NW * P * KR + 4 * (size_t)(Nc + 1) + 16 +
+    return (size_t)2 * nst * KR * 256 + (size_t)2 * NW * P * KR + 4 * (size_t)(Nc + RP_SINK) + 16 +
            10 * RP_MAXK + 16 + 4 * RP_MAXK + 24 + 16 + 10 * 8 + 16;
 }
 
@@ -813,7 +833,8 @@ void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
     nw = 2;
     kernel = rowpass_kernel(P, fp16);
     KR = ((A.nexc + 15) / 16) * 16;
-    if (!kernel || KR > RP_MAXK || A.ns > 32766 || B.ns > 32766)
+    // 15-bit targets: every string index and sink cell (ns + 31) below 2^15
+    if (!kernel || KR > RP_MAXK || A.ns > 32768 - RP_SINK || B.ns > 32768 - RP_SINK)
         KPM_THROW(KPM_EUNSUPPORTED, "tensor-core sigma supports up to 16 orbitals");
     int dev = 0;
     KPM_CUDA(cudaGetDevice(&dev));
@@ -861,7 +882,7 @@ void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
     auto build_slots = [&](const SpinTables& T, DevBuf& out) {
         size_t count = (size_t)P * T.ns;
         out.alloc(count * sizeof(uint16_t));
-        k_slot_fill<<<1024, 256, 0, st>>>(out.as<uint16_t>(), (int64_t)count, (uint16_t)T.ns);
+        k_slot_fill<<<1024, 256, 0, st>>>(out.as<uint16_t>(), (int64_t)count, T.ns);
         KPM_LAUNCHED();
         int64_t ne = T.ns * T.nexc;
         if (ne > 0) {
