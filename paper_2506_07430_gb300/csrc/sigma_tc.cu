@@ -106,6 +106,10 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
+// hint: bring `bytes` (multiple of 16, 16-byte aligned) at p into L2
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 
 // Shared-memory matrix descriptor, canonical layouts without swizzle: 8 x 16-byte
 // core matrices (128 contiguous bytes); LBO = byte distance between core
@@ -172,6 +176,7 @@ constexpr int RP_MMA_WARP = RP_SCATTER_WARPS + RP_COPY_WARPS;   // MMA issue (on
 constexpr int RP_WARPS = RP_SCATTER_WARPS + RP_COPY_WARPS + 1;
 constexpr int RP_THREADS = 32 * RP_WARPS;
 constexpr int RP_MAXK = 96;                  // largest KR: 9 * 10 = 90 entries rounded up
+static_assert(RP_COPY_WARPS * 32 >= RP_MAXK, "one copy lane per entry (L2 prefetch)");
 // sink cells after the row's sigma: an absent slot of column J targets cell
 // Nc + (J mod 32), so the scatter adds every slot without a branch and the 32
 // lanes of a warp (32 consecutive J) sink into 32 different banks
@@ -185,6 +190,11 @@ constexpr int RP_SHIFT = 2;
 // about one scatter duration of slack, microseconds)
 #ifndef RP_BACKOFF_NS
 #define RP_BACKOFF_NS 256
+#endif
+// the copy warps prefetch the A rows of tile t + RP_PREFETCH into L2 when they
+// copy tile t (a quarter of the gathered segments miss L2; 0: no prefetch)
+#ifndef RP_PREFETCH
+#define RP_PREFETCH 4
 #endif
 constexpr uint32_t A_LBO = 2048;             // A stage: K-group (8 entries) stride, bytes
 constexpr uint32_t A_SBO = 128;              // A stage: MN-group (8 columns) stride, bytes
@@ -523,6 +533,16 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
                     if (!ok) break;
                 }
                 copies(t, gt % nst);
+                if (RP_PREFETCH > 0 && t + RP_PREFETCH < ntiles) {
+                    // entry cw * 32 + lane: both pieces of its 128 columns (256 bytes each)
+                    const int e = cw * 32 + lane;
+                    const int64_t ro = e < KR ? rowoff[e] : -1;
+                    if (ro >= 0) {
+                        const int64_t off = ro + (int64_t)(t + RP_PREFETCH) * 128;
+                        prefetch_l2(p.Xh + off, 256u);
+                        prefetch_l2(p.Xl + off, 256u);
+                    }
+                }
                 if (t >= 1) publish(gt - 1, true);
             }
             if (ok && ntiles > 0) publish(g + (uint32_t)ntiles - 1, false);
@@ -832,7 +852,9 @@ void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
     fp16 = use_fp16;
     nw = 2;
     kernel = rowpass_kernel(P, fp16);
-    KR = ((A.nexc + 15) / 16) * 16;
+    // at least one K step: a row without entries (no alpha electrons) then multiplies
+    // padding (B_R = 0) and D is exactly zero instead of never written
+    KR = A.nexc > 0 ? ((A.nexc + 15) / 16) * 16 : 16;
     // 15-bit targets: every string index and sink cell (ns + 31) below 2^15
     if (!kernel || KR > RP_MAXK || A.ns > 32768 - RP_SINK || B.ns > 32768 - RP_SINK)
         KPM_THROW(KPM_EUNSUPPORTED, "tensor-core sigma supports up to 16 orbitals");
