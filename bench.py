@@ -40,7 +40,7 @@ UNIT = "steps/s"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # dominant kernel, from one ncu capture of the current kernel (summarised in
 # profiles/k_rowpass_fci16o16e.md); absent (null) where no capture exists.
-NCU_TRAFFIC_BYTES = {("fci16o16e", "mixed"): 12.3920e9 + 0.66031e9}
+NCU_TRAFFIC_BYTES = {("fci16o16e", "mixed"): 12.389437696e9 + 0.660145920e9}
 
 
 def parse_args():
