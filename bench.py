@@ -70,6 +70,11 @@ def parse_args():
     p.add_argument("--graphs-compare", type=int, default=0, metavar="NSTEPS",
                    help="time NSTEPS Chebyshev steps of --workload/--precision with the steps "
                         "replayed from CUDA graphs and issued kernel by kernel")
+    p.add_argument("--batch-small", type=int, default=0, metavar="K",
+                   help="spectra/s of K small molecules (8o-10o, FP32): one batched launch "
+                        "per Chebyshev step against one request at a time")
+    p.add_argument("--batch-moments", type=int, default=512, metavar="N",
+                   help="moments per molecule for --batch-small")
     p.add_argument("--accuracy", type=int, default=0, metavar="NMOMENTS",
                    help="per-moment error of --precision (and fp32) against the FP64 path on "
                         "--workload for NMOMENTS moments, dipole component z")
@@ -474,6 +479,58 @@ def run_graphs_compare(args):
     return out
 
 
+def run_batch_small(args):
+    """Spectra/s for K small molecules (--batch-small K, sizes cycling through 8o,
+    9o and 10o half filling, 3 dipole components, --batch-moments moments, FP32):
+    one kpm_moments_batch call against one kpm_moments call per molecule (each
+    with its CUDA-graph steps); moments must agree bit for bit.  Inputs resident;
+    the rescaling comes from each context's Lanczos bounds (150 steps, 5 % margin)
+    outside the timing."""
+    import torch
+
+    from paper_2506_07430_gb300 import KPM, moments_batch
+
+    torch.cuda.set_device(0)
+    K = int(args.batch_small)
+    N = int(args.batch_moments)
+    sizes = [(8, 4, 4), (9, 4, 5), (10, 5, 5)]
+    ks, psis, a, b = [], [], [], []
+    for i in range(K):
+        n, na, nb = sizes[i % len(sizes)]
+        I = synthetic.integrals(n, na, nb, 2506400 + i)
+        k = KPM(I.h1, I.eri, I.dipole, n, na, nb, precision="fp32")
+        lo, hi = k.bounds(iters=150, seed=2506001)
+        ai, bi = KPM.scale(lo, hi, eps=0.05)   # margin for FP32 vectors over N moments
+        ks.append(k)
+        psis.append(torch.from_numpy(synthetic.random_state(k.dim, 2506500 + i)).cuda())
+        a.append(ai)
+        b.append(bi)
+    for _ in range(2):                       # warm-up (graph capture, scratch allocation)
+        seq = [k.moments(p, 0b111, ai, bi, N) for k, p, ai, bi in zip(ks, psis, a, b)]
+        bat = moments_batch(ks, psis, 0b111, a, b, N)
+    torch.cuda.synchronize()
+    reps = 3
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        seq = [k.moments(p, 0b111, ai, bi, N) for k, p, ai, bi in zip(ks, psis, a, b)]
+    t_seq = (time.perf_counter() - t0) / reps
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        bat = moments_batch(ks, psis, 0b111, a, b, N)
+    t_bat = (time.perf_counter() - t0) / reps
+    same = all(np.array_equal(bat[i], seq[i]) for i in range(K))
+    for k in ks:
+        k.close()
+    return {"metric": "spectra/s, K small molecules: one batched launch per step vs one "
+                      "request at a time",
+            "config": {"molecules": K, "sizes": [list(sizes[i % 3]) for i in range(K)],
+                       "nmoments": N, "components": 3, "precision": "fp32",
+                       "timing": "host wall clock of the synchronous calls, mean of 3"},
+            "batched": {"spectra_per_s": round(K / t_bat, 3), "s_per_batch": round(t_bat, 4)},
+            "one_at_a_time": {"spectra_per_s": round(K / t_seq, 3), "s_total": round(t_seq, 4)},
+            "speedup": round(t_seq / t_bat, 3), "moments_identical": same}
+
+
 def run_accuracy(args):
     """Moments of one seeded request on --workload in FP64 (the reference: its parity
     with the oracle is tested at 8o-12o and on sampled rows at 14o-18o) and in the
@@ -672,6 +729,9 @@ def main():
         return
     if args.graphs_compare:
         print(json.dumps(run_graphs_compare(args)), flush=True)
+        return
+    if args.batch_small:
+        print(json.dumps(run_batch_small(args)), flush=True)
         return
     if args.impl == "reference":
         # rank 0 alone times the oracle; other ranks exit without work

@@ -176,6 +176,30 @@ kpm_status kpm_moments_host(kpm_ctx* ctx, const double* psi0_host, unsigned comp
                             double a, double b, int nmoments, double* moments_host);
 
 /*
+ * kpm_moments_batch -- kpm_moments for `count` molecules at once: after each
+ * molecule's first step, every further Chebyshev step of all molecules is one
+ * sigma launch and one update launch over a flattened grid (a table of the
+ * molecules' operands, with each molecule's own reduction grid), so small
+ * molecules do not pay one set of launches each.  Per molecule the arithmetic
+ * and reduction order are those of kpm_moments: the moments are identical.
+ *   ctxs       [count] distinct contexts, all KPM_FP64 or all KPM_FP32 (the
+ *              CUDA-core gather path), on one device.
+ *   psi0_dev   [count] FP64 device ground states, psi0_dev[i] of ctxs[i]'s dim.
+ *   a, b       [count] host rescaling of each molecule (as kpm_moments).
+ *   moments_host  host [count][popcount(comp_mask)][nmoments].
+ * All work runs on ctxs[0]'s stream (the others' streams are synchronised
+ * first); each context's recursion state is left as after kpm_moments.
+ * Synchronous.  Errors: KPM_EINVAL for NULL or repeated contexts, mixed or
+ * tensor-core (KPM_MIXED*) precisions, or invalid a, b, nmoments, comp_mask;
+ * KPM_EBOUNDS if some molecule's |Omega_n| > Omega_0 (1 + 1e-6) (all moments
+ * still written; kpm_last_error(ctxs[i]) names it).  The paper's serving
+ * pattern of many small molecules per launch; Eq. moments, Methods recursion.
+ */
+kpm_status kpm_moments_batch(kpm_ctx* const* ctxs, int count, const double* const* psi0_dev,
+                             unsigned comp_mask, const double* a, const double* b, int nmoments,
+                             double* moments_host);
+
+/*
  * Resumable recursion (the same computation as kpm_moments, in pieces):
  *   kpm_recursion_begin  alpha_0 = mu psi0, first step; state kept on device.
  *   kpm_recursion_advance  `nsteps` further Chebyshev steps (asynchronous).

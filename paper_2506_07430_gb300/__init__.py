@@ -15,8 +15,9 @@ from ._lib import (  # noqa: F401
     launch_count,
     library_path,
     load_library,
+    moments_batch,
     spectrum,
 )
 
-__all__ = ["KPM", "KPMError", "PRECISIONS", "Server", "spectrum", "launch_count", "load_library",
-           "library_path"]
+__all__ = ["KPM", "KPMError", "PRECISIONS", "Server", "moments_batch", "spectrum", "launch_count",
+           "load_library", "library_path"]

@@ -33,6 +33,7 @@ SIGNATURES = {
     "kpm_scale": (None, [_D, _D, _D, _P, _P]),
     "kpm_moments": (_I, [_P, _P, _U, _D, _D, _I, _P]),
     "kpm_moments_host": (_I, [_P, _P, _U, _D, _D, _I, _P]),
+    "kpm_moments_batch": (_I, [_P, _I, _P, _U, _P, _P, _I, _P]),
     "kpm_recursion_begin": (_I, [_P, _P, _U, _D, _D, _I]),
     "kpm_recursion_advance": (_I, [_P, _I]),
     "kpm_recursion_moments": (_I, [_P, _P, _P]),
@@ -337,6 +338,29 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def moments_batch(kpms, psi0s, comp_mask: int, a, b, nmoments: int, check_bounds: bool = True):
+    """Moments of several molecules in batched launches (kpm_moments_batch).
+
+    kpms: FP64 or FP32 KPM contexts (one precision); psi0s: CUDA float64 tensors;
+    a, b: per-molecule rescaling.  Returns [len(kpms), ncomp, nmoments]."""
+    import torch
+    count = len(kpms)
+    if count == 0 or len(psi0s) != count or len(a) != count or len(b) != count:
+        raise ValueError("kpms, psi0s, a and b need the same non-zero length")
+    ncomp = bin(comp_mask).count("1")
+    out = np.zeros((count, ncomp, nmoments), np.float64)
+    ctxs = (ctypes.c_void_p * count)(*[k._h for k in kpms])
+    psis = (ctypes.c_void_p * count)(*[_dev_ptr(p, torch.float64) for p in psi0s])
+    av = np.ascontiguousarray(a, dtype=np.float64)
+    bv = np.ascontiguousarray(b, dtype=np.float64)
+    st = load_library().kpm_moments_batch(ctxs, count, psis, comp_mask, _np_ptr(av), _np_ptr(bv),
+                                          nmoments, _np_ptr(out))
+    if st == KPM_EBOUNDS and not check_bounds:
+        return out
+    _check(st, kpms[0]._h)
+    return out
 
 
 def spectrum(moments, a: float, b: float, npoints: int = 2048, kernel: str = "jackson"):

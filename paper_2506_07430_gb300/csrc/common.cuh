@@ -134,6 +134,55 @@ void dipole_apply_f64(const SpinTables& ta, const SpinTables& tb, const double* 
 void dipole_apply_f32(const SpinTables& ta, const SpinTables& tb, const double* d_dip,
                       const double* psi, float* y, cudaStream_t st);
 
+// ---------------------------------------------------------------- batched steps
+
+// One molecule of a batched recursion step (kpm_moments_batch): the operands of
+// its sigma and update work and its first block in each flattened grid.  All
+// molecules of a batch share the path (FP64, or FP32 with the exact diagonal).
+struct BatchMol {
+    // sigma: y = H x (gather path), x and y [ncol][nsa * nsb]
+    const void* x;
+    void* y;
+    int64_t nsa, nsb;
+    const int32_t* tgtA;
+    const uint16_t* pqA;
+    const int8_t* sgnA;
+    const int32_t* fcolA;
+    const void* fvalA;
+    const int32_t* tgtBT;
+    const uint16_t* pqBT;
+    const int8_t* sgnBT;
+    const int32_t* fcolB;
+    const void* fvalB;
+    const void* V;
+    const float2* diag;
+    int nexcA, nnbrA, nexcB, nnbrB, n, ncol;
+    // update: prev <- 2 (y - b x) / a - prev; dots of step n at dots[col * dstride + 2n]
+    void* prev;
+    double a, b;
+    double* partials;
+    unsigned* counters;
+    double* dots;
+    int64_t dstride;
+    int nblk;           // reduction blocks per column: reduce_blocks(nsa * nsb)
+    int64_t sblk0;      // first block of this molecule in the flattened sigma grid
+    int64_t ublk0;      // first block of this molecule in the flattened update grid
+};
+
+// Sigma of every molecule of mols[0 .. nmol) in one launch of `blocks` blocks
+// (sum over molecules of ceil(nsb / 128) * nsa * ncol); smem: the largest
+// per-molecule staging size.  Per element the same arithmetic as sigma_gather_*.
+void sigma_gather_batch_f64(const BatchMol* mols, int nmol, int64_t blocks, size_t smem,
+                            cudaStream_t st);
+void sigma_gather_batch_f32(const BatchMol* mols, int nmol, int64_t blocks, size_t smem,
+                            cudaStream_t st);
+// Non-first update of every molecule in one launch (blocks = sum of nblk * ncol),
+// dots of step n; per element and per reduction the same as cheb_update_*.
+void cheb_update_batch_f64(const BatchMol* mols, int nmol, int64_t blocks, int n,
+                           cudaStream_t st);
+void cheb_update_batch_f32(const BatchMol* mols, int nmol, int64_t blocks, int n,
+                           cudaStream_t st);
+
 // ---------------------------------------------------------------- recursion helpers
 
 // Fixed reduction grid for a vector of length dim (deterministic partial order).

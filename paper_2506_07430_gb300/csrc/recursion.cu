@@ -49,16 +49,16 @@ __device__ __forceinline__ void block_sum2(double& u, double& v) {
     }
 }
 
-// Stores the block partials; the last block of column `col` sums them in a
-// fixed order into out[0], out[1] and re-arms the counter.
+// Stores the partials of block blk (of nblk); the last block to finish sums
+// them in a fixed order into out[0], out[1] and re-arms the counter.
 __device__ __forceinline__ void finish_reduce(double u, double v, double* partials,
-                                              unsigned* counter, int nblk, double* out0,
+                                              unsigned* counter, int nblk, int blk, double* out0,
                                               double* out1) {
     block_sum2(u, v);
     __shared__ bool last;
     if (threadIdx.x == 0) {
-        partials[2 * blockIdx.x] = u;
-        partials[2 * blockIdx.x + 1] = v;
+        partials[2 * blk] = u;
+        partials[2 * blk + 1] = v;
         __threadfence();
         unsigned prev = atomicAdd(counter, 1u);
         last = (prev == (unsigned)nblk - 1);
@@ -79,23 +79,25 @@ __device__ __forceinline__ void finish_reduce(double u, double v, double* partia
     }
 }
 
+// Block blk (of nblk) of column col of the update; dots of step n go to
+// dots[2n], dots[2n+1].  Shared by the single-molecule kernel and the batched
+// one, so that both do the same arithmetic and reduction.
 template <class T>
-__global__ void __launch_bounds__(RED_THREADS)
-k_cheb_update(const T* __restrict__ s, const T* __restrict__ c, T* __restrict__ prev, int64_t dim,
-              double a, double b, int first, double* partials, unsigned* counters, double* dots,
-              int64_t dstride, const unsigned* step) {
-    const int col = blockIdx.y;
-    // dots of step n go to dots[2n], dots[2n+1]; n from the device counter if given
-    if (step) dots += 2 * (int64_t)(*step);
+__device__ __forceinline__ void cheb_update_cta(int blk, int nblk, int col,
+                                                const T* __restrict__ s, const T* __restrict__ c,
+                                                T* __restrict__ prev, int64_t dim, double a,
+                                                double b, int first, double* partials,
+                                                unsigned* counters, double* dots, int64_t dstride,
+                                                int64_t n) {
+    dots += 2 * n;
     s += col * dim;
     c += col * dim;
     prev += col * dim;
-    const int nblk = gridDim.x;
     const int64_t stride = (int64_t)nblk * blockDim.x;
     double ss = 0.0, tt = 0.0;
     if constexpr (sizeof(T) == 8) {
         const double k1 = (first ? 1.0 : 2.0) / a, k2 = b * k1;
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim; i += stride) {
+        for (int64_t i = (int64_t)blk * blockDim.x + threadIdx.x; i < dim; i += stride) {
             double cv = c[i];
             double nx = k1 * s[i] - k2 * cv;
             if (!first) nx -= prev[i];
@@ -105,7 +107,7 @@ k_cheb_update(const T* __restrict__ s, const T* __restrict__ c, T* __restrict__ 
         }
     } else {
         const float k1 = (float)((first ? 1.0 : 2.0) / a), k2 = (float)(b * (first ? 1.0 : 2.0) / a);
-        int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        int64_t i = (int64_t)blk * blockDim.x + threadIdx.x;
         while (i < dim) {
             float gs = 0.f, gt = 0.f;
 #pragma unroll
@@ -124,8 +126,58 @@ k_cheb_update(const T* __restrict__ s, const T* __restrict__ c, T* __restrict__ 
             tt += (double)gt;
         }
     }
-    finish_reduce(ss, tt, partials + (int64_t)col * 2 * nblk, counters + col, nblk,
+    finish_reduce(ss, tt, partials + (int64_t)col * 2 * nblk, counters + col, nblk, blk,
                   dots + col * dstride, dots + col * dstride + 1);
+}
+
+template <class T>
+__global__ void __launch_bounds__(RED_THREADS)
+k_cheb_update(const T* __restrict__ s, const T* __restrict__ c, T* __restrict__ prev, int64_t dim,
+              double a, double b, int first, double* partials, unsigned* counters, double* dots,
+              int64_t dstride, const unsigned* step) {
+    // n from the device counter if given (replayable captured steps), else 0
+    const int64_t n = step ? (int64_t)(*step) : 0;
+    cheb_update_cta<T>(blockIdx.x, gridDim.x, blockIdx.y, s, c, prev, dim, a, b, first, partials,
+                       counters, dots, dstride, n);
+}
+
+// Batched non-first update: the flattened grid covers every molecule's
+// (reduction block, column) blocks; each molecule keeps its own fixed
+// reduction grid, partials and counters.
+template <class T>
+__global__ void __launch_bounds__(RED_THREADS)
+k_cheb_update_batch(const BatchMol* __restrict__ mols, int nmol, int64_t n) {
+    const int64_t blk = blockIdx.x;
+    int lo = 0, hi = nmol - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (mols[mid].ublk0 <= blk) lo = mid; else hi = mid - 1;
+    }
+    const BatchMol& m = mols[lo];
+    const int64_t local = blk - m.ublk0;
+    const int b = (int)(local % m.nblk);
+    const int col = (int)(local / m.nblk);
+    cheb_update_cta<T>(b, m.nblk, col, static_cast<const T*>(m.y), static_cast<const T*>(m.x),
+                       static_cast<T*>(m.prev), m.nsa * m.nsb, m.a, m.b, 0, m.partials,
+                       m.counters, m.dots, m.dstride, n);
+}
+
+template <class T>
+static void launch_update_batch(const BatchMol* mols, int nmol, int64_t blocks, int n,
+                                cudaStream_t st) {
+    if (nmol <= 0 || blocks <= 0) return;
+    if (blocks > 0x7FFFFFFFLL) KPM_THROW(KPM_EINVAL, "batched update grid too large");
+    k_cheb_update_batch<T><<<(unsigned)blocks, RED_THREADS, 0, st>>>(mols, nmol, (int64_t)n);
+    KPM_LAUNCHED();
+}
+
+void cheb_update_batch_f64(const BatchMol* mols, int nmol, int64_t blocks, int n,
+                           cudaStream_t st) {
+    launch_update_batch<double>(mols, nmol, blocks, n, st);
+}
+void cheb_update_batch_f32(const BatchMol* mols, int nmol, int64_t blocks, int n,
+                           cudaStream_t st) {
+    launch_update_batch<float>(mols, nmol, blocks, n, st);
 }
 
 template <class T>
@@ -196,7 +248,7 @@ k_dot(const T* __restrict__ x, const T* __restrict__ y, int64_t dim, double* par
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim; i += stride)
         u += (double)x[i] * (double)y[i];
-    finish_reduce(u, v, partials, counter, gridDim.x, out, nullptr);
+    finish_reduce(u, v, partials, counter, gridDim.x, blockIdx.x, out, nullptr);
 }
 
 void dot_dev(const void* x, const void* y, int64_t dim, bool f64, double* partials,
@@ -227,7 +279,7 @@ k_lanczos_orth(T* __restrict__ w, const T* __restrict__ v, const T* __restrict__
         w[i] = xt;
         u += (double)xt * (double)xt;
     }
-    finish_reduce(u, 0.0, partials, counter, gridDim.x, norm2, nullptr);
+    finish_reduce(u, 0.0, partials, counter, gridDim.x, blockIdx.x, norm2, nullptr);
 }
 
 void lanczos_orth(void* w, const void* v, const void* vprev, int64_t dim, bool f64,

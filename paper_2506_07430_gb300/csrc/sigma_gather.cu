@@ -27,15 +27,18 @@ namespace kpm {
 // and beta excitations are both diagonal (p == q).  Large diagonal energies
 // then carry no FP32 representation error, which would otherwise shift every
 // eigenvalue systematically and grow the moment error linearly in n.
+// One CTA of the gather sigma: beta tile bx (128 strings), alpha string ia,
+// column col.  Shared by the single-molecule kernel and the batched one, so that
+// both do the same arithmetic per element.
 template <class T, bool EXACT_DIAG>
-__global__ void __launch_bounds__(128)
-k_sigma_gather(const T* __restrict__ x, T* __restrict__ y, int64_t nsa, int64_t nsb,
-               const int32_t* __restrict__ tgtA, const uint16_t* __restrict__ pqA,
-               const int8_t* __restrict__ sgnA, int nexcA, const int32_t* __restrict__ fcolA,
-               const T* __restrict__ fvalA, int nnbrA, const int32_t* __restrict__ tgtBT,
-               const uint16_t* __restrict__ pqBT, const int8_t* __restrict__ sgnBT, int nexcB,
-               const int32_t* __restrict__ fcolB, const T* __restrict__ fvalB, int nnbrB,
-               const T* __restrict__ V, int n, const float2* __restrict__ diag) {
+__device__ __forceinline__ void sigma_gather_cta(
+    int64_t bx, int64_t ia, int64_t col, const T* __restrict__ x, T* __restrict__ y, int64_t nsa,
+    int64_t nsb, const int32_t* __restrict__ tgtA, const uint16_t* __restrict__ pqA,
+    const int8_t* __restrict__ sgnA, int nexcA, const int32_t* __restrict__ fcolA,
+    const T* __restrict__ fvalA, int nnbrA, const int32_t* __restrict__ tgtBT,
+    const uint16_t* __restrict__ pqBT, const int8_t* __restrict__ sgnBT, int nexcB,
+    const int32_t* __restrict__ fcolB, const T* __restrict__ fvalB, int nnbrB,
+    const T* __restrict__ V, int n, const float2* __restrict__ diag) {
     extern __shared__ __align__(16) unsigned char smem[];
     T* sFv = reinterpret_cast<T*>(smem);
     int32_t* sFc = reinterpret_cast<int32_t*>(sFv + nnbrA);
@@ -45,11 +48,10 @@ k_sigma_gather(const T* __restrict__ x, T* __restrict__ y, int64_t nsa, int64_t 
     __shared__ int sNoff;
 
     const int n2 = n * n;
-    const int64_t ia = blockIdx.y;
-    const int64_t ib = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t ib = bx * blockDim.x + threadIdx.x;
     const int64_t dim = nsa * nsb;
-    x += (int64_t)blockIdx.z * dim;
-    y += (int64_t)blockIdx.z * dim;
+    x += col * dim;
+    y += col * dim;
 
     for (int t = threadIdx.x; t < nnbrA; t += blockDim.x) {
         sFv[t] = fvalA[(int64_t)t * nsa + ia];
@@ -111,6 +113,45 @@ k_sigma_gather(const T* __restrict__ x, T* __restrict__ y, int64_t nsa, int64_t 
     y[ia * nsb + ib] = acc;
 }
 
+template <class T, bool EXACT_DIAG>
+__global__ void __launch_bounds__(128)
+k_sigma_gather(const T* __restrict__ x, T* __restrict__ y, int64_t nsa, int64_t nsb,
+               const int32_t* __restrict__ tgtA, const uint16_t* __restrict__ pqA,
+               const int8_t* __restrict__ sgnA, int nexcA, const int32_t* __restrict__ fcolA,
+               const T* __restrict__ fvalA, int nnbrA, const int32_t* __restrict__ tgtBT,
+               const uint16_t* __restrict__ pqBT, const int8_t* __restrict__ sgnBT, int nexcB,
+               const int32_t* __restrict__ fcolB, const T* __restrict__ fvalB, int nnbrB,
+               const T* __restrict__ V, int n, const float2* __restrict__ diag) {
+    sigma_gather_cta<T, EXACT_DIAG>(blockIdx.x, blockIdx.y, blockIdx.z, x, y, nsa, nsb, tgtA, pqA,
+                                    sgnA, nexcA, fcolA, fvalA, nnbrA, tgtBT, pqBT, sgnBT, nexcB,
+                                    fcolB, fvalB, nnbrB, V, n, diag);
+}
+
+// Batched gather sigma: the flattened grid covers every molecule's
+// (beta tile, alpha string, column) blocks; a block finds its molecule by binary
+// search over the molecules' first blocks.
+template <class T, bool EXACT_DIAG>
+__global__ void __launch_bounds__(128)
+k_sigma_gather_batch(const BatchMol* __restrict__ mols, int nmol) {
+    const int64_t blk = blockIdx.x;
+    int lo = 0, hi = nmol - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (mols[mid].sblk0 <= blk) lo = mid; else hi = mid - 1;
+    }
+    const BatchMol& m = mols[lo];
+    const int64_t tiles = (m.nsb + 127) / 128;
+    const int64_t local = blk - m.sblk0;
+    const int64_t bx = local % tiles;
+    const int64_t ia = (local / tiles) % m.nsa;
+    const int64_t col = local / (tiles * m.nsa);
+    sigma_gather_cta<T, EXACT_DIAG>(
+        bx, ia, col, static_cast<const T*>(m.x), static_cast<T*>(m.y), m.nsa, m.nsb, m.tgtA,
+        m.pqA, m.sgnA, m.nexcA, m.fcolA, static_cast<const T*>(m.fvalA), m.nnbrA, m.tgtBT,
+        m.pqBT, m.sgnBT, m.nexcB, m.fcolB, static_cast<const T*>(m.fvalB), m.nnbrB,
+        static_cast<const T*>(m.V), m.n, m.diag);
+}
+
 template <class T, bool ED>
 static void launch_sigma(const SigmaArgs& a, const T* x, T* y, int ncol, const T* fvA,
                          const T* fvB, cudaStream_t st) {
@@ -128,6 +169,27 @@ static void launch_sigma(const SigmaArgs& a, const T* x, T* y, int ncol, const T
         B.sgnT.as<int8_t>(), B.nexc, B.fcol.as<int32_t>(), fvB, B.nnbr,
         static_cast<const T*>(a.V), a.n, a.diag);
     KPM_LAUNCHED();
+}
+
+template <class T, bool ED>
+static void launch_sigma_batch(const BatchMol* mols, int nmol, int64_t blocks, size_t smem,
+                               cudaStream_t st) {
+    if (nmol <= 0 || blocks <= 0) return;
+    if (blocks > 0x7FFFFFFFLL) KPM_THROW(KPM_EINVAL, "batched sigma grid too large");
+    if (smem > 48 * 1024)
+        KPM_CUDA(cudaFuncSetAttribute(k_sigma_gather_batch<T, ED>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_sigma_gather_batch<T, ED><<<(unsigned)blocks, 128, smem, st>>>(mols, nmol);
+    KPM_LAUNCHED();
+}
+
+void sigma_gather_batch_f64(const BatchMol* mols, int nmol, int64_t blocks, size_t smem,
+                            cudaStream_t st) {
+    launch_sigma_batch<double, false>(mols, nmol, blocks, smem, st);
+}
+void sigma_gather_batch_f32(const BatchMol* mols, int nmol, int64_t blocks, size_t smem,
+                            cudaStream_t st) {
+    launch_sigma_batch<float, true>(mols, nmol, blocks, smem, st);
 }
 
 void sigma_gather_f64(const SigmaArgs& a, const double* x, double* y, int ncol, cudaStream_t st) {
