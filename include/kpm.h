@@ -187,8 +187,9 @@ kpm_status kpm_moments_host(kpm_ctx* ctx, const double* psi0_host, unsigned comp
  *   psi0_dev   [count] FP64 device ground states, psi0_dev[i] of ctxs[i]'s dim.
  *   a, b       [count] host rescaling of each molecule (as kpm_moments).
  *   moments_host  host [count][popcount(comp_mask)][nmoments].
- * All work runs on ctxs[0]'s stream (the others' streams are synchronised
- * first); each context's recursion state is left as after kpm_moments.
+ * Each molecule's first step runs on its own context's stream, the batched
+ * steps on ctxs[0]'s stream, ordered between them by CUDA events; each
+ * context's recursion state is left as after kpm_moments.
  * Synchronous.  Errors: KPM_EINVAL for NULL or repeated contexts, mixed or
  * tensor-core (KPM_MIXED*) precisions, or invalid a, b, nmoments, comp_mask;
  * KPM_EBOUNDS if some molecule's |Omega_n| > Omega_0 (1 + 1e-6) (all moments
@@ -211,6 +212,18 @@ kpm_status kpm_recursion_begin(kpm_ctx* ctx, const double* psi0_dev, unsigned co
                                double a, double b, int max_moments);
 kpm_status kpm_recursion_advance(kpm_ctx* ctx, int nsteps);
 kpm_status kpm_recursion_moments(kpm_ctx* ctx, double* moments_host, int* nmoments_out);
+
+/*
+ * kpm_recursion_advance_batch -- kpm_recursion_advance(ctxs[i], nsteps) for
+ * every context, as one sigma launch and one update launch per Chebyshev step
+ * for all of them (the batched path of kpm_moments_batch; the contexts may be at
+ * different steps).  The launches go to ctxs[0]'s stream, ordered after the
+ * work already queued on each context's stream and before work queued on it
+ * later (CUDA events): asynchronous.  The result of each recursion is identical
+ * to advancing it alone.  Errors: KPM_EINVAL as kpm_moments_batch, or if some
+ * context has no recursion in progress or would pass its max_moments.
+ */
+kpm_status kpm_recursion_advance_batch(kpm_ctx* const* ctxs, int count, int nsteps);
 
 /*
  * kpm_spectrum -- Jackson-damped (kernel=1) or undamped (kernel=0) Chebyshev

@@ -16,8 +16,9 @@ from ._lib import (  # noqa: F401
     library_path,
     load_library,
     moments_batch,
+    recursion_advance_batch,
     spectrum,
 )
 
-__all__ = ["KPM", "KPMError", "PRECISIONS", "Server", "moments_batch", "spectrum", "launch_count",
-           "load_library", "library_path"]
+__all__ = ["KPM", "KPMError", "PRECISIONS", "Server", "moments_batch", "recursion_advance_batch",
+           "spectrum", "launch_count", "load_library", "library_path"]

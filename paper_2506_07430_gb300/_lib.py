@@ -36,6 +36,7 @@ SIGNATURES = {
     "kpm_moments_batch": (_I, [_P, _I, _P, _U, _P, _P, _I, _P]),
     "kpm_recursion_begin": (_I, [_P, _P, _U, _D, _D, _I]),
     "kpm_recursion_advance": (_I, [_P, _I]),
+    "kpm_recursion_advance_batch": (_I, [_P, _I, _I]),
     "kpm_recursion_moments": (_I, [_P, _P, _P]),
     "kpm_spectrum": (_I, [_P, _I, _D, _D, _I, _I, _P, _P]),
     "kpm_synchronize": (_I, [_P]),
@@ -361,6 +362,16 @@ def moments_batch(kpms, psi0s, comp_mask: int, a, b, nmoments: int, check_bounds
         return out
     _check(st, kpms[0]._h)
     return out
+
+
+def recursion_advance_batch(kpms, nsteps: int):
+    """kpm_recursion_advance_batch: advance every context's resumable recursion
+    by nsteps in batched launches (asynchronous)."""
+    count = len(kpms)
+    if count == 0:
+        raise ValueError("empty context list")
+    ctxs = (ctypes.c_void_p * count)(*[k._h for k in kpms])
+    _check(load_library().kpm_recursion_advance_batch(ctxs, count, nsteps), kpms[0]._h)
 
 
 def spectrum(moments, a: float, b: float, npoints: int = 2048, kernel: str = "jackson"):

@@ -51,7 +51,14 @@ struct kpm_ctx {
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     uint64_t glaunches[2] = {0, 0};   // kernels in one replay (launch accounting)
     DevBuf step_ctr;                  // unsigned: index n of the next step's dots
-    DevBuf batch_desc;                // BatchMol tables of kpm_moments_batch (first context)
+    // batched steps led by this context: device BatchMol tables, their pinned
+    // staging copy (reused once the event of the previous upload has passed), and
+    // an event that orders this context's stream against a batch's stream
+    DevBuf batch_desc;
+    BatchMol* desc_host = nullptr;
+    size_t desc_host_cap = 0;
+    cudaEvent_t ev_desc = nullptr;
+    cudaEvent_t ev_order = nullptr;
     cudaStream_t cap_st = nullptr;    // private stream for capture (any user stream may be
                                       // the legacy default stream, which cannot be captured)
     void drop_graphs() {
@@ -65,6 +72,9 @@ struct kpm_ctx {
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
         drop_graphs();
         if (cap_st) cudaStreamDestroy(cap_st);
+        if (ev_desc) cudaEventDestroy(ev_desc);
+        if (ev_order) cudaEventDestroy(ev_order);
+        if (desc_host) cudaFreeHost(desc_host);
     }
 
     size_t esz() const { return prec == KPM_FP64 ? 8 : 4; }
@@ -303,6 +313,130 @@ void rec_advance(kpm_ctx* c, int nsteps) {
         step_direct(c);
         ++k;
     }
+}
+
+// Batched steps (kpm_moments_batch, kpm_recursion_advance_batch): contexts of
+// one batch are distinct, on one device, all on the gather path (FP64 or FP32).
+void check_batch(kpm_ctx* const* ctxs, int count) {
+    const kpm_ctx* c0 = ctxs[0];
+    for (int i = 0; i < count; ++i) {
+        const kpm_ctx* c = ctxs[i];
+        if (!c) KPM_THROW(KPM_EINVAL, "context %d is NULL", i);
+        if (c->prec != KPM_FP64 && c->prec != KPM_FP32)
+            KPM_THROW(KPM_EINVAL, "batched steps run the gather path: FP64 or FP32 contexts "
+                                  "only (context %d)", i);
+        if (c->prec != c0->prec) KPM_THROW(KPM_EINVAL, "contexts of a batch share one precision");
+        if (c->device != c0->device) KPM_THROW(KPM_EINVAL, "contexts of a batch share one device");
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == c) KPM_THROW(KPM_EINVAL, "context %d appears twice", i);
+    }
+}
+
+cudaEvent_t order_event(kpm_ctx* c) {
+    if (!c->ev_order) KPM_CUDA(cudaEventCreateWithFlags(&c->ev_order, cudaEventDisableTiming));
+    return c->ev_order;
+}
+
+// nsteps Chebyshev steps of every context's recursion (each mid-recursion, at its
+// own step) as one sigma and one update launch per step on ctxs[0]'s stream,
+// ordered after each context's queued work and before its later work by events.
+void batch_steps(kpm_ctx* const* ctxs, int count, int nsteps) {
+    if (nsteps <= 0) return;
+    kpm_ctx* c0 = ctxs[0];
+    cudaStream_t st = c0->st;
+    for (int i = 1; i < count; ++i)
+        if (ctxs[i]->st != st) {
+            KPM_CUDA(cudaEventRecord(order_event(ctxs[i]), ctxs[i]->st));
+            KPM_CUDA(cudaStreamWaitEvent(st, ctxs[i]->ev_order, 0));
+        }
+    const bool f64 = c0->prec == KPM_FP64;
+    // operand tables for the two assignments of the rotating vectors, staged in
+    // pinned memory (the previous upload from it must have been read first)
+    const size_t need = (size_t)2 * count;
+    if (c0->ev_desc) KPM_CUDA(cudaEventSynchronize(c0->ev_desc));
+    else KPM_CUDA(cudaEventCreateWithFlags(&c0->ev_desc, cudaEventDisableTiming));
+    if (c0->desc_host_cap < need) {
+        if (c0->desc_host) cudaFreeHost(c0->desc_host);
+        c0->desc_host = nullptr;
+        c0->desc_host_cap = 0;
+        KPM_CUDA(cudaMallocHost(&c0->desc_host, need * sizeof(BatchMol)));
+        c0->desc_host_cap = need;
+    }
+    BatchMol* h = c0->desc_host;
+    int64_t sblk = 0, ublk = 0;
+    size_t smem = 16;
+    for (int i = 0; i < count; ++i) {
+        kpm_ctx* c = ctxs[i];
+        const SpinTables& A = c->ta;
+        const SpinTables& B = *c->tb;
+        BatchMol m{};
+        m.nsa = A.ns;
+        m.nsb = B.ns;
+        m.tgtA = A.tgt.as<int32_t>();
+        m.pqA = A.pq.as<uint16_t>();
+        m.sgnA = A.sgn.as<int8_t>();
+        m.fcolA = A.fcol.as<int32_t>();
+        m.fvalA = f64 ? A.fval64.p : A.fval32.p;
+        m.tgtBT = B.tgtT.as<int32_t>();
+        m.pqBT = B.pqT.as<uint16_t>();
+        m.sgnBT = B.sgnT.as<int8_t>();
+        m.fcolB = B.fcol.as<int32_t>();
+        m.fvalB = f64 ? B.fval64.p : B.fval32.p;
+        m.V = f64 ? c->d_eri.p : c->d_V32.p;
+        m.diag = f64 ? nullptr : c->d_diag.as<float2>();
+        m.nexcA = A.nexc;
+        m.nnbrA = A.nnbr;
+        m.nexcB = B.nexc;
+        m.nnbrB = B.nnbr;
+        m.n = c->n;
+        m.ncol = c->rec_ncol;
+        m.a = c->rec_a;
+        m.b = c->rec_b;
+        m.partials = c->partials.as<double>();
+        m.counters = c->counters.as<unsigned>();
+        m.dots = c->dots.as<double>();
+        m.dstride = (int64_t)c->rec_max_steps * 2;
+        m.step0 = c->rec_steps;
+        m.nblk = reduce_blocks(c->dim);
+        m.sblk0 = sblk;
+        m.ublk0 = ublk;
+        sblk += (B.ns + 127) / 128 * A.ns * m.ncol;
+        ublk += (int64_t)m.nblk * m.ncol;
+        smem = std::max(smem, (size_t)A.nnbr * ((f64 ? 8 : 4) + 4) + (size_t)A.nexc * 12 + 16);
+        // even batch steps: the current assignment; odd: swapped
+        m.x = c->rec_cur;
+        m.y = c->vS.p;
+        m.prev = c->rec_prev;
+        h[i] = m;
+        m.x = c->rec_prev;
+        m.prev = c->rec_cur;
+        h[(size_t)count + i] = m;
+    }
+    c0->batch_desc.ensure(need * sizeof(BatchMol));
+    KPM_CUDA(cudaMemcpyAsync(c0->batch_desc.p, h, need * sizeof(BatchMol), cudaMemcpyHostToDevice,
+                             st));
+    KPM_CUDA(cudaEventRecord(c0->ev_desc, st));
+    const BatchMol* d = c0->batch_desc.as<BatchMol>();
+    for (int k = 0; k < nsteps; ++k) {
+        const BatchMol* dk = d + (size_t)(k & 1) * count;
+        if (f64) {
+            sigma_gather_batch_f64(dk, count, sblk, smem, st);
+            cheb_update_batch_f64(dk, count, ublk, k, st);
+        } else {
+            sigma_gather_batch_f32(dk, count, sblk, smem, st);
+            cheb_update_batch_f32(dk, count, ublk, k, st);
+        }
+    }
+    for (int i = 0; i < count; ++i) {
+        kpm_ctx* c = ctxs[i];
+        if (nsteps & 1) std::swap(c->rec_prev, c->rec_cur);
+        c->rec_steps += nsteps;
+        // device step counter for later graph-replayed steps of this context
+        step_set(c->step_ctr.as<unsigned>(), (unsigned)c->rec_steps, st);
+    }
+    KPM_CUDA(cudaEventRecord(order_event(c0), st));
+    for (int i = 1; i < count; ++i)
+        if (ctxs[i]->st != st) KPM_CUDA(cudaStreamWaitEvent(ctxs[i]->st, c0->ev_order, 0));
 }
 
 void check_device_errors(kpm_ctx* c) {
@@ -570,104 +704,13 @@ kpm_status kpm_moments_batch(kpm_ctx* const* ctxs, int count, const double* cons
     }
     kpm_ctx* c0 = ctxs[0];
     kpm_status r = KPM_OK;
-    std::vector<cudaStream_t> saved;
     kpm_status s = guarded(c0, [&] {
         if (!psi0_dev || !a || !b || !moments_host) KPM_THROW(KPM_EINVAL, "NULL argument");
-        for (int i = 0; i < count; ++i) {
-            kpm_ctx* c = ctxs[i];
-            if (!c) KPM_THROW(KPM_EINVAL, "context %d is NULL", i);
-            if (c->prec != KPM_FP64 && c->prec != KPM_FP32)
-                KPM_THROW(KPM_EINVAL, "batched steps run the gather path: FP64 or FP32 contexts "
-                                      "only (context %d)", i);
-            if (c->prec != c0->prec) KPM_THROW(KPM_EINVAL, "contexts of a batch share one precision");
-            if (c->device != c0->device) KPM_THROW(KPM_EINVAL, "contexts of a batch share one device");
-            for (int j = 0; j < i; ++j)
-                if (ctxs[j] == c) KPM_THROW(KPM_EINVAL, "context %d appears twice", i);
-        }
+        check_batch(ctxs, count);
         DeviceGuard g(c0->device);
-        // every molecule's work in order on the first context's stream
-        for (int i = 0; i < count; ++i) saved.push_back(ctxs[i]->st);
-        for (int i = 1; i < count; ++i) {
-            if (ctxs[i]->st != c0->st) KPM_CUDA(cudaStreamSynchronize(ctxs[i]->st));
-            ctxs[i]->st = c0->st;
-        }
-        const bool f64 = c0->prec == KPM_FP64;
         for (int i = 0; i < count; ++i)
             rec_begin(ctxs[i], psi0_dev[i], comp_mask, a[i], b[i], nmoments);
-        const int nsteps = nmoments / 2 - 1;
-        if (nsteps > 0) {
-            // operand tables for the two assignments of the rotating vectors
-            std::vector<BatchMol> h((size_t)2 * count);
-            int64_t sblk = 0, ublk = 0;
-            size_t smem = 16;
-            for (int i = 0; i < count; ++i) {
-                kpm_ctx* c = ctxs[i];
-                const SpinTables& A = c->ta;
-                const SpinTables& B = *c->tb;
-                BatchMol m{};
-                m.nsa = A.ns;
-                m.nsb = B.ns;
-                m.tgtA = A.tgt.as<int32_t>();
-                m.pqA = A.pq.as<uint16_t>();
-                m.sgnA = A.sgn.as<int8_t>();
-                m.fcolA = A.fcol.as<int32_t>();
-                m.fvalA = f64 ? A.fval64.p : A.fval32.p;
-                m.tgtBT = B.tgtT.as<int32_t>();
-                m.pqBT = B.pqT.as<uint16_t>();
-                m.sgnBT = B.sgnT.as<int8_t>();
-                m.fcolB = B.fcol.as<int32_t>();
-                m.fvalB = f64 ? B.fval64.p : B.fval32.p;
-                m.V = f64 ? c->d_eri.p : c->d_V32.p;
-                m.diag = f64 ? nullptr : c->d_diag.as<float2>();
-                m.nexcA = A.nexc;
-                m.nnbrA = A.nnbr;
-                m.nexcB = B.nexc;
-                m.nnbrB = B.nnbr;
-                m.n = c->n;
-                m.ncol = c->rec_ncol;
-                m.a = c->rec_a;
-                m.b = c->rec_b;
-                m.partials = c->partials.as<double>();
-                m.counters = c->counters.as<unsigned>();
-                m.dots = c->dots.as<double>();
-                m.dstride = (int64_t)c->rec_max_steps * 2;
-                m.nblk = reduce_blocks(c->dim);
-                m.sblk0 = sblk;
-                m.ublk0 = ublk;
-                sblk += (B.ns + 127) / 128 * A.ns * m.ncol;
-                ublk += (int64_t)m.nblk * m.ncol;
-                smem = std::max(smem, (size_t)A.nnbr * ((f64 ? 8 : 4) + 4) + (size_t)A.nexc * 12 + 16);
-                // even steps: as left by the first step; odd steps: swapped
-                m.x = c->rec_cur;
-                m.y = c->vS.p;
-                m.prev = c->rec_prev;
-                h[i] = m;
-                m.x = c->rec_prev;
-                m.prev = c->rec_cur;
-                h[(size_t)count + i] = m;
-            }
-            c0->batch_desc.ensure(h.size() * sizeof(BatchMol));
-            KPM_CUDA(cudaMemcpyAsync(c0->batch_desc.p, h.data(), h.size() * sizeof(BatchMol),
-                                     cudaMemcpyHostToDevice, c0->st));
-            const BatchMol* d = c0->batch_desc.as<BatchMol>();
-            for (int k = 0; k < nsteps; ++k) {
-                const BatchMol* dk = d + (size_t)(k & 1) * count;
-                if (f64) {
-                    sigma_gather_batch_f64(dk, count, sblk, smem, c0->st);
-                    cheb_update_batch_f64(dk, count, ublk, 1 + k, c0->st);
-                } else {
-                    sigma_gather_batch_f32(dk, count, sblk, smem, c0->st);
-                    cheb_update_batch_f32(dk, count, ublk, 1 + k, c0->st);
-                }
-            }
-            for (int i = 0; i < count; ++i) {
-                kpm_ctx* c = ctxs[i];
-                if (nsteps & 1) std::swap(c->rec_prev, c->rec_cur);
-                c->rec_steps += nsteps;
-                step_set(c->step_ctr.as<unsigned>(), (unsigned)c->rec_steps, c->st);
-            }
-            // the host table is copied before cudaMemcpyAsync returns (pageable source)
-        }
+        batch_steps(ctxs, count, nmoments / 2 - 1);
         const int ncomp = __builtin_popcount(comp_mask);
         for (int i = 0; i < count; ++i) {
             kpm_status ri = rec_collect(ctxs[i], moments_host + (size_t)i * ncomp * nmoments,
@@ -675,8 +718,25 @@ kpm_status kpm_moments_batch(kpm_ctx* const* ctxs, int count, const double* cons
             if (r == KPM_OK) r = ri;
         }
     });
-    for (size_t i = 0; i < saved.size(); ++i) ctxs[i]->st = saved[i];
     return s != KPM_OK ? s : r;
+}
+
+kpm_status kpm_recursion_advance_batch(kpm_ctx* const* ctxs, int count, int nsteps) {
+    if (!ctxs || count < 1 || !ctxs[0]) {
+        g_err = "NULL or empty context list";
+        return KPM_EINVAL;
+    }
+    return guarded(ctxs[0], [&] {
+        check_batch(ctxs, count);
+        for (int i = 0; i < count; ++i) {
+            const kpm_ctx* c = ctxs[i];
+            if (c->rec_steps <= 0) KPM_THROW(KPM_EINVAL, "context %d: no recursion in progress", i);
+            if (nsteps < 0 || c->rec_steps + nsteps > c->rec_max_steps)
+                KPM_THROW(KPM_EINVAL, "context %d: advance past the requested number of moments", i);
+        }
+        DeviceGuard g(ctxs[0]->device);
+        batch_steps(ctxs, count, nsteps);
+    });
 }
 
 kpm_status kpm_moments_host(kpm_ctx* ctx, const double* psi0_host, unsigned comp_mask, double a,

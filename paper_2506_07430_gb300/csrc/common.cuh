@@ -157,13 +157,15 @@ struct BatchMol {
     const void* V;
     const float2* diag;
     int nexcA, nnbrA, nexcB, nnbrB, n, ncol;
-    // update: prev <- 2 (y - b x) / a - prev; dots of step n at dots[col * dstride + 2n]
+    // update: prev <- 2 (y - b x) / a - prev; dots of step n at dots[col * dstride + 2n],
+    // n = step0 + (the step's index within the batch)
     void* prev;
     double a, b;
     double* partials;
     unsigned* counters;
     double* dots;
     int64_t dstride;
+    int64_t step0;      // recursion steps done before the batch
     int nblk;           // reduction blocks per column: reduce_blocks(nsa * nsb)
     int64_t sblk0;      // first block of this molecule in the flattened sigma grid
     int64_t ublk0;      // first block of this molecule in the flattened update grid
@@ -177,10 +179,11 @@ void sigma_gather_batch_f64(const BatchMol* mols, int nmol, int64_t blocks, size
 void sigma_gather_batch_f32(const BatchMol* mols, int nmol, int64_t blocks, size_t smem,
                             cudaStream_t st);
 // Non-first update of every molecule in one launch (blocks = sum of nblk * ncol),
-// dots of step n; per element and per reduction the same as cheb_update_*.
-void cheb_update_batch_f64(const BatchMol* mols, int nmol, int64_t blocks, int n,
+// batch step k (dots of step step0 + k); per element and per reduction the same
+// as cheb_update_*.
+void cheb_update_batch_f64(const BatchMol* mols, int nmol, int64_t blocks, int k,
                            cudaStream_t st);
-void cheb_update_batch_f32(const BatchMol* mols, int nmol, int64_t blocks, int n,
+void cheb_update_batch_f32(const BatchMol* mols, int nmol, int64_t blocks, int k,
                            cudaStream_t st);
 
 // ---------------------------------------------------------------- recursion helpers

@@ -146,7 +146,7 @@ k_cheb_update(const T* __restrict__ s, const T* __restrict__ c, T* __restrict__ 
 // reduction grid, partials and counters.
 template <class T>
 __global__ void __launch_bounds__(RED_THREADS)
-k_cheb_update_batch(const BatchMol* __restrict__ mols, int nmol, int64_t n) {
+k_cheb_update_batch(const BatchMol* __restrict__ mols, int nmol, int64_t k) {
     const int64_t blk = blockIdx.x;
     int lo = 0, hi = nmol - 1;
     while (lo < hi) {
@@ -159,25 +159,25 @@ k_cheb_update_batch(const BatchMol* __restrict__ mols, int nmol, int64_t n) {
     const int col = (int)(local / m.nblk);
     cheb_update_cta<T>(b, m.nblk, col, static_cast<const T*>(m.y), static_cast<const T*>(m.x),
                        static_cast<T*>(m.prev), m.nsa * m.nsb, m.a, m.b, 0, m.partials,
-                       m.counters, m.dots, m.dstride, n);
+                       m.counters, m.dots, m.dstride, m.step0 + k);
 }
 
 template <class T>
-static void launch_update_batch(const BatchMol* mols, int nmol, int64_t blocks, int n,
+static void launch_update_batch(const BatchMol* mols, int nmol, int64_t blocks, int k,
                                 cudaStream_t st) {
     if (nmol <= 0 || blocks <= 0) return;
     if (blocks > 0x7FFFFFFFLL) KPM_THROW(KPM_EINVAL, "batched update grid too large");
-    k_cheb_update_batch<T><<<(unsigned)blocks, RED_THREADS, 0, st>>>(mols, nmol, (int64_t)n);
+    k_cheb_update_batch<T><<<(unsigned)blocks, RED_THREADS, 0, st>>>(mols, nmol, (int64_t)k);
     KPM_LAUNCHED();
 }
 
-void cheb_update_batch_f64(const BatchMol* mols, int nmol, int64_t blocks, int n,
+void cheb_update_batch_f64(const BatchMol* mols, int nmol, int64_t blocks, int k,
                            cudaStream_t st) {
-    launch_update_batch<double>(mols, nmol, blocks, n, st);
+    launch_update_batch<double>(mols, nmol, blocks, k, st);
 }
-void cheb_update_batch_f32(const BatchMol* mols, int nmol, int64_t blocks, int n,
+void cheb_update_batch_f32(const BatchMol* mols, int nmol, int64_t blocks, int k,
                            cudaStream_t st) {
-    launch_update_batch<float>(mols, nmol, blocks, n, st);
+    launch_update_batch<float>(mols, nmol, blocks, k, st);
 }
 
 template <class T>

@@ -11,15 +11,18 @@
 // are combined (doubling identities), its spectrum is reconstructed on its
 // stream, and its context is released, which frees budget for the queue.
 //
-// Every request's arithmetic runs on its own context with the same kernels and
-// launch shapes it would use alone, so its result does not depend on what else
-// is resident.  All waits are bounded (kpm_server_wait's timeout; the worker's
+// Every request's arithmetic is what it would be alone: its own context, the
+// same kernels, launch shapes and reduction grids (on the FP64 / FP32 gather
+// path, requests that advance by the same number of steps in a round share
+// batched launches whose per-request work is that of the single launches), so
+// its result does not depend on what else is resident.  All waits are bounded (kpm_server_wait's timeout; the worker's
 // condition-variable waits).
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <thread>
@@ -215,11 +218,30 @@ void kpm_server::run() {
                 mem_used -= s->req->mem;
             }
         }
-        // one round: queue every resident request's steps before waiting on any
+        // one round: queue every resident request's steps before waiting on any.
+        // On the gather path (FP64, FP32) the requests that advance by the same
+        // number of steps share one sigma and one update launch per step
+        // (kpm_recursion_advance_batch); each result is identical either way.
+        const bool gather = cfg.precision == KPM_FP64 || cfg.precision == KPM_FP32;
+        std::map<int, std::vector<Slot*>> by_k;
         for (auto& s : active) {
             if (s->req->cancelled) continue;
             int k = std::min(cfg.steps_per_round, s->total - s->steps);
-            if (k > 0 && kpm_recursion_advance(s->ctx, k) == KPM_OK) s->steps += k;
+            if (k <= 0) continue;
+            if (gather) by_k[k].push_back(s.get());
+            else if (kpm_recursion_advance(s->ctx, k) == KPM_OK) s->steps += k;
+        }
+        for (auto& kv : by_k) {
+            const int k = kv.first;
+            std::vector<Slot*>& group = kv.second;
+            if (group.size() == 1) {
+                if (kpm_recursion_advance(group[0]->ctx, k) == KPM_OK) group[0]->steps += k;
+                continue;
+            }
+            std::vector<kpm_ctx*> ctxs;
+            for (Slot* s : group) ctxs.push_back(s->ctx);
+            if (kpm_recursion_advance_batch(ctxs.data(), (int)ctxs.size(), k) == KPM_OK)
+                for (Slot* s : group) s->steps += k;
         }
         std::vector<std::unique_ptr<Slot>> keep;
         for (auto& s : active) {

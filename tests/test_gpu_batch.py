@@ -132,3 +132,30 @@ def test_batch_rejects_bad_lists(torch):
     assert np.array_equal(out[0], ks[0].moments(psis[0], 1, a[0], b[0], 40))
     for k in ks + [k32, kmx]:
         k.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_advance_batch_at_different_steps(torch, prec):
+    """Resumable recursions at different steps, advanced together in chunks (with
+    single-context advances in between), equal the same recursions advanced alone."""
+    from paper_2506_07430_gb300 import recursion_advance_batch
+    mols = [(6, 3, 3), (8, 4, 4), (7, 2, 4)]
+    ks, psis, ab, _ = _batch(torch, prec, mols, seed0=2506380)
+    N = 80
+    ref = [k.moments(p, 0b101, a, b, N) for k, p, (a, b) in zip(ks, psis, ab)]
+    for k, p, (a, b) in zip(ks, psis, ab):
+        k.recursion_begin(p, 0b101, a, b, N)
+    ks[1].recursion_advance(3)
+    ks[2].recursion_advance(6)
+    recursion_advance_batch(ks, 7)              # steps 1..7, 4..10, 7..13
+    ks[0].recursion_advance(5)                  # single (graph) steps after a batch
+    recursion_advance_batch(ks[1:], 20)
+    for k in ks:                                # the rest alone: 27, 9 and 6 steps
+        done = k.recursion_moments().shape[1] // 2
+        k.recursion_advance(N // 2 - done)
+    for i, k in enumerate(ks):
+        got = k.recursion_moments()
+        assert got.shape == (2, N)
+        assert np.array_equal(got, ref[i]), (i, np.abs(got - ref[i]).max())
+    for k in ks:
+        k.close()

@@ -82,6 +82,8 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.kpm_moments_batch(None, 0, None, 1, None, None, 4, None) == 1
     two_null = (ctypes.c_void_p * 2)(None, None)
     assert lib.kpm_moments_batch(two_null, 2, None, 1, None, None, 4, None) == 1
+    assert lib.kpm_recursion_advance_batch(None, 1, 4) == 1
+    assert lib.kpm_recursion_advance_batch(two_null, 2, 4) == 1
     a, b = ctypes.c_double(), ctypes.c_double()
     lib.kpm_scale(-3.0, 5.0, 0.01, ctypes.byref(a), ctypes.byref(b))
     assert abs(a.value - 8.0 / 1.99) < 1e-15 and b.value == 1.0

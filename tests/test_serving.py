@@ -39,8 +39,10 @@ def _submit(srv, case, mask=0b111):
     return srv.submit(I.h1, I.eri, I.dipole, n, m, m, psi, mask, a, b, nm, npoints=256)
 
 
-@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("prec", ["mixed", "fp64", "fp32"])
 def test_same_alone_and_in_mix(cases, prec):
+    """In the mix, FP64 / FP32 requests that advance by the same number of steps
+    share batched launches; alone, each runs its own."""
     from paper_2506_07430_gb300 import Server
     srv = Server(mem_budget_bytes=4 << 30, max_slots=4, steps_per_round=8, precision=prec)
     alone = []
