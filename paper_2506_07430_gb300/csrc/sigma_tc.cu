@@ -302,14 +302,17 @@ __device__ __forceinline__ bool wait_phase(uint64_t* mbar, uint32_t parity, vola
 // poll theirs with a sleep in between, leaving the issue slots to the scatter):
 //   copy (warps 16-18, a third of the copies each): copies of tile t into
 //     stage t % nst once MMA(t - nst) has released it; once they have landed
-//     (and been fenced for the async proxy), each arrives on "A full";
+//     (and been fenced for the async proxy), each arrives on "A full"; with
+//     them, one lane per entry prefetches that entry's rows of tile
+//     t + RP_PREFETCH into L2;
 //   MMA (warp 19, one thread): MMA(t) once A(t) is full and the scatter warps
 //     have released D buffer t & 1; tcgen05.commit then signals "stage free"
 //     and "D full";
 //   scatter (warps 0-15, 4 per TMEM lane quadrant, one column J per thread):
 //     wait for D(t), copy it to registers, release the D buffer, and add every
-//     present slot into the row's sigma in shared memory with 32-bit
-//     fixed-point atomics (order-independent: bitwise reproducible).  The 4
+//     slot into the row's sigma in shared memory with 32-bit fixed-point
+//     atomics (order-independent: bitwise reproducible; an absent slot adds
+//     into the lane's sink cell after the row, so there is no branch).  The 4
 //     warps of a quadrant share the NS used slots evenly (chunks of 8
 //     round-robin, the remaining chunks split in pairs of slots).
 // Rows are separated by CTA barriers (set-up of the next row's B_R and sigma).
@@ -319,9 +322,10 @@ __device__ __forceinline__ bool wait_phase(uint64_t* mbar, uint32_t parity, vola
 // R, |D[J][s]| <= c_s = sum_e rowmax(tgt_e) |W[slot e][s]| (rowmax: max |x| of a
 // source row), which sets the row's a-priori scale (capped so that B_R stays in
 // range); vectors with small or empty source rows get a correspondingly finer
-// step.  The first launch runs at a scale 2^shift finer than that bound; the scatter warps track max |D| per row, and a row that
-// reaches the limit is not written but appended to a list that the second
-// launch (shift = 0, rows from the list) recomputes.  Which rows take the
+// step.  The first launch runs at a scale 2^shift finer than that bound; the
+// scatter warps track max |D| per row, and a row that reaches the limit is not
+// written but appended to a list that the second launch (shift = 0, rows from
+// the list) recomputes.  Which rows take the
 // second pass depends only on the data, so results stay reproducible.
 template <int P, bool FP16, int NW>
 __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
