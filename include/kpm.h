@@ -222,6 +222,7 @@ kpm_status kpm_recursion_moments(kpm_ctx* ctx, double* moments_host, int* nmomen
  * later (CUDA events): asynchronous.  The result of each recursion is identical
  * to advancing it alone.  Errors: KPM_EINVAL as kpm_moments_batch, or if some
  * context has no recursion in progress or would pass its max_moments.
+ * Paper: Methods, KPM recursion; the serving pattern of many molecules per launch.
  */
 kpm_status kpm_recursion_advance_batch(kpm_ctx* const* ctxs, int count, int nsteps);
 

@@ -109,3 +109,12 @@ def test_binding_refuses_missing_library(tmp_path, monkeypatch):
     monkeypatch.setattr(L, "_LIBPATH", str(tmp_path / "nope.so"))
     with pytest.raises(RuntimeError, match="no fallback"):
         L.load_library()
+
+
+def test_batch_bindings_validate_lists_before_any_call():
+    import paper_2506_07430_gb300 as pkg
+    with pytest.raises(ValueError):
+        pkg.moments_batch([], [], 1, [], [], 4)
+    with pytest.raises(ValueError):
+        pkg.recursion_advance_batch([], 4)
+
