@@ -63,6 +63,8 @@ def _lib():
             lib.sc_sigma_rows.argtypes = [P, P, I64, P, P]
             lib.sc_sigma.restype = None
             lib.sc_sigma.argtypes = [P, P, P]
+            lib.sc_sigma_block.restype = None
+            lib.sc_sigma_block.argtypes = [P, P, P, ctypes.c_int]
             lib.sc_row_counts.restype = None
             lib.sc_row_counts.argtypes = [P, P]
             lib.sc_fill_csr.restype = None
@@ -155,6 +157,17 @@ class SlaterCondon:
         y = np.empty(self.dim, np.float64)
         _lib().sc_sigma(self._cp(), _ptr(x), _ptr(y))
         return y
+
+    def sigma_block(self, X):
+        """Y[c] = H X[c] for a block X of shape (ncol, dim): each row of H is
+        generated once for all columns (the same per-column sums as ``sigma``)."""
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        assert X.ndim == 2 and X.shape[1] == self.dim
+        if self._csr is not None:
+            return np.ascontiguousarray((self._csr @ X.T).T)
+        Y = np.empty_like(X)
+        _lib().sc_sigma_block(self._cp(), _ptr(X), _ptr(Y), X.shape[0])
+        return Y
 
     def csr(self) -> sp.csr_matrix:
         """Full sparse H (dims up to a few 1e5 only)."""

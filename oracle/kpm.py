@@ -33,7 +33,8 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["jackson", "moments_recursion", "moments_direct", "moments_eigen",
+__all__ = ["jackson", "moments_recursion", "moments_recursion_block", "moments_direct",
+           "moments_eigen",
            "chebyshev_nodes", "spectrum", "spectrum_eigen", "scale_from_bounds"]
 
 
@@ -75,6 +76,26 @@ def moments_recursion(apply_h, alpha0: np.ndarray, a: float, b: float, nmoments:
         prev, cur = cur, nxt
     if return_direct:
         return mu, np.array(direct)
+    return mu
+
+
+def moments_recursion_block(apply_h_block, alpha0, a: float, b: float, nmoments: int):
+    """``moments_recursion`` for several start vectors at once (rows of ``alpha0``,
+    shape (ncol, dim)); ``apply_h_block(V)`` returns H V row by row.  Every column
+    runs the same recursion and doubling identities; returns (ncol, nmoments)."""
+    if nmoments < 2 or nmoments % 2:
+        raise ValueError("nmoments must be even and >= 2")
+    a0 = np.array(alpha0, np.float64, ndmin=2)
+    a1 = (apply_h_block(a0) - b * a0) / a
+    mu = np.empty((a0.shape[0], nmoments))
+    mu[:, 0] = np.einsum("ij,ij->i", a0, a0)
+    mu[:, 1] = np.einsum("ij,ij->i", a1, a0)
+    prev, cur = a0, a1
+    for n in range(1, nmoments // 2):
+        nxt = 2.0 * (apply_h_block(cur) - b * cur) / a - prev
+        mu[:, 2 * n] = 2.0 * np.einsum("ij,ij->i", cur, cur) - mu[:, 0]
+        mu[:, 2 * n + 1] = 2.0 * np.einsum("ij,ij->i", nxt, cur) - mu[:, 1]
+        prev, cur = cur, nxt
     return mu
 
 

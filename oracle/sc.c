@@ -221,6 +221,31 @@ void sc_sigma(const sc_system* S, const double* x, double* y) {
     }
 }
 
+/* Y[c] = H X[c] for ncol columns stored one after the other ([ncol][dim]): each
+ * row of H is generated once and applied to every column; per column the sum
+ * is the one sc_sigma forms, term for term in the same order. */
+void sc_sigma_block(const sc_system* S, const double* X, double* Y, int ncol) {
+    int64_t dim = S->nsa * S->nsb;
+    int64_t cap = sc_row_capacity(S);
+#pragma omp parallel
+    {
+        int64_t* cols = (int64_t*)malloc(sizeof(int64_t) * cap);
+        double* vals = (double*)malloc(sizeof(double) * cap);
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t r = 0; r < dim; ++r) {
+            int64_t k = sc_row(S, r, cols, vals);
+            for (int c = 0; c < ncol; ++c) {
+                const double* x = X + (int64_t)c * dim;
+                double acc = 0.0;
+                for (int64_t t = 0; t < k; ++t) acc += vals[t] * x[cols[t]];
+                Y[(int64_t)c * dim + r] = acc;
+            }
+        }
+        free(cols);
+        free(vals);
+    }
+}
+
 /* Number of stored entries of each row (for a CSR build). */
 void sc_row_counts(const sc_system* S, int64_t* counts) {
     int64_t dim = S->nsa * S->nsb;

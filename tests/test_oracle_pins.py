@@ -351,6 +351,64 @@ def test_moments_closed_form_without_two_body():
     assert np.abs(mu - ref).max() < 1e-12 * ref[0]
 
 
+def test_spectral_bounds_contain_dense_spectrum_8o():
+    """ARPACK bounds widened by their Ritz residuals against LAPACK's dense
+    eigenvalues (a different routine): they contain the spectrum and are tight."""
+    I, sc, H, E, U = _system8()
+    lo, hi = oracle.spectral_bounds(sc.sigma, sc.dim)
+    width = E[-1] - E[0]
+    assert lo <= E[0] and hi >= E[-1], (lo, hi, E[0], E[-1])
+    assert E[0] - lo < 1e-8 * width and hi - E[-1] < 1e-8 * width
+
+
+def test_spectral_bounds_10o_against_plain_lanczos_residuals():
+    """10 orbitals (FCI dim 63,504): the extreme Ritz pairs of a plain Lanczos
+    iteration with full reorthogonalisation written here (independent of ARPACK's
+    implicitly restarted one), with residuals recomputed by the Slater-Condon
+    row-pull, lie within the bounds and within their residual of them (an
+    eigenvalue lies within |r| of a Ritz value theta)."""
+    import scipy.linalg as sl
+    I = synthetic.integrals(10, 5, 5, 2506100)
+    sc = oracle.SlaterCondon(I.h1, I.eri, 10, 5, 5)
+    H = sc.csr()
+    lo, hi = oracle.spectral_bounds(sc.sigma, sc.dim)
+    k = 160
+    Q = np.zeros((k + 1, sc.dim))
+    al, be = np.zeros(k), np.zeros(k)
+    q = np.random.default_rng(3).standard_normal(sc.dim)
+    Q[0] = q / np.linalg.norm(q)
+    for j in range(k):
+        w = H @ Q[j]
+        al[j] = Q[j] @ w
+        w -= Q[: j + 1].T @ (Q[: j + 1] @ w)            # full reorthogonalisation, twice
+        w -= Q[: j + 1].T @ (Q[: j + 1] @ w)
+        be[j] = np.linalg.norm(w)
+        Q[j + 1] = w / be[j]
+    th, S = sl.eigh_tridiagonal(al, be[:-1])
+    for idx, bound, sgn in ((0, lo, 1.0), (k - 1, hi, -1.0)):
+        x = Q[:k].T @ S[:, idx]
+        x /= np.linalg.norm(x)
+        r = np.linalg.norm(sc.sigma(x) - th[idx] * x)      # row-pull, not the CSR
+        assert r < 1e-6, r
+        assert sgn * (th[idx] + sgn * r - bound) >= 0.0, (bound, th[idx], r)
+        assert abs(th[idx] - bound) < 1e-6 * (hi - lo), (bound, th[idx])
+
+
+def test_block_recursion_equals_column_recursion():
+    """moments_recursion_block runs the column recursion on every column of a block
+    (H rows generated once per block by the row-pull)."""
+    I, sc, H, E, U = _system8()
+    a, b = kpm.scale_from_bounds(E[0], E[-1])
+    A0 = np.stack([sc.dipole(I.dipole[c], U[:, 0]) for c in range(3)])
+    Y = sc.sigma_block(A0)
+    for c in range(3):
+        assert np.array_equal(Y[c], sc.sigma(A0[c]))
+    mb = kpm.moments_recursion_block(sc.sigma_block, A0, a, b, 128)
+    for c in range(3):
+        mc = kpm.moments_recursion(sc.sigma, A0[c], a, b, 128)
+        assert np.abs(mb[c] - mc).max() < 1e-13 * mc[0]
+
+
 # ---------------------------------------------------------------- planted mistakes
 
 def test_planted_transposed_eri_is_caught():
