@@ -38,9 +38,29 @@ METRIC = "Chebyshev steps/s at 16o/16e"
 UNIT = "steps/s"
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# dominant kernel, from one ncu capture of the current kernel (summarised in
-# profiles/k_rowpass_fci16o16e.md); absent (null) where no capture exists.
-NCU_TRAFFIC_BYTES = {("fci16o16e", "mixed"): 12.389437696e9 + 0.660145920e9}
+# dominant kernel from one ncu capture (summarised under profiles/), with the
+# SHA-256 (first 16 hex digits) of the kernel's source file at the time of the
+# capture: the bench reports the figure only while that source is unchanged,
+# else null (the counters describe another kernel).
+NCU_TRAFFIC = {}
+
+
+def _source_sha16(rel):
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            return hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+
+
+def ncu_traffic(workload, precision):
+    rec = NCU_TRAFFIC.get((workload, precision))
+    if rec is None:
+        return None, "no ncu capture of the current kernel"
+    if _source_sha16(rec["source"]) != rec["source_sha16"]:
+        return None, f"kernel source changed since the ncu capture of {rec['captured']}"
+    return rec["bytes"], f"ncu capture {rec['captured']} ({rec['profile']})"
 
 
 def parse_args():
@@ -53,7 +73,17 @@ def parse_args():
     p.add_argument("--precision", choices=["fp64", "fp32", "mixed", "mixed_bf16"], default="mixed")
     p.add_argument("--chunk", type=int, default=None, help="Chebyshev steps per bench step")
     p.add_argument("--lanczos", type=int, default=24, help="Lanczos steps for a, b (untimed)")
-    p.add_argument("--e2e-requests", type=int, default=2)
+    p.add_argument("--state", choices=["ground", "random"], default="ground",
+                   help="start vector psi0: the GPU ground state (default) or a seeded random state")
+    p.add_argument("--gs-iters", type=int, default=30, help="Lanczos steps per ground-state cycle")
+    p.add_argument("--gs-cycles", type=int, default=3, help="ground-state restart cycles")
+    p.add_argument("--gs-tol", type=float, default=1e-4, help="ground-state residual target")
+    p.add_argument("--e2e-requests", type=int, default=1)
+    p.add_argument("--e2e-moments", type=int, default=256,
+                   help="moments per end-to-end request (kpm_moments_host)")
+    p.add_argument("--check-steps", type=int, default=12,
+                   help="Chebyshev steps of the same recursion run on the FP64 path (untimed) "
+                        "to report the per-moment error of the timed precision")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--sigma-only", type=int, default=0,
@@ -79,6 +109,11 @@ def parse_args():
                    help="per-moment error of --precision (and fp32) against the FP64 path on "
                         "--workload for NMOMENTS moments, dipole component z")
     p.add_argument("--serve-budget-gb", type=float, default=8.0)
+    p.add_argument("--convergence", type=int, default=0, metavar="NMAX",
+                   help="spectrum convergence with the number of moments on --workload: "
+                        "spectra from the first N = 256 ... NMAX moments of one deflated "
+                        "recursion of --precision on the GPU ground state, against the FP64 "
+                        "path at every N; prints one JSON line")
     return p.parse_args()
 
 
@@ -257,9 +292,21 @@ def run_ours(args, ws, rank, local, pg):
     I = synthetic.integrals(n, na, nb, w["seed"])
     k = KPM(I.h1, I.eri, I.dipole, n, na, nb, precision=args.precision)
     dim = k.dim
-    # Ground-state stand-in: a seeded normalised FP64 vector (per rank).
-    psi0_host = synthetic.random_state(dim, 2506000 + rank)
-    psi0 = torch.from_numpy(psi0_host).cuda()
+    # Ground state |0> of the workload from the library's restarted Lanczos on the
+    # same context (untimed); --state random uses a seeded normalised vector instead.
+    gs = None
+    if args.state == "ground":
+        t0 = time.perf_counter()
+        e0, res, psi0 = k.ground_state(iters=args.gs_iters, max_cycles=args.gs_cycles,
+                                       tol=args.gs_tol, seed=2506002 + rank)
+        torch.cuda.synchronize()
+        gs = {"e0": e0, "residual": res, "seconds": round(time.perf_counter() - t0, 2),
+              "iters_per_cycle": args.gs_iters, "max_cycles": args.gs_cycles,
+              "method": "kpm_ground_state (restarted Lanczos, H in the bench precision)"}
+        psi0_host = psi0.cpu().numpy()
+    else:
+        psi0_host = synthetic.random_state(dim, 2506000 + rank)
+        psi0 = torch.from_numpy(psi0_host).cuda()
     emin, emax = k.bounds(iters=args.lanczos, seed=2506001)
     a, b = KPM.scale(emin, emax)
     comp = 0b100
@@ -296,7 +343,23 @@ def run_ours(args, ws, rank, local, pg):
     steps_all = sum_over_ranks(float(chunk * steps), pg)
     value = steps_all / (ms_max / 1e3)
     mom = k.recursion_moments()
-    moments_ok = bool(np.all(np.abs(mom) <= mom[:, :1] * (1 + 1e-6)))
+    bounded = bool(np.all(np.abs(mom) <= mom[:, :1] * (1 + 1e-6)))
+
+    # accuracy of the timed precision: the first moments of the same recursion
+    # (same psi0, a, b) on the FP64 path, untimed
+    acc = None
+    if args.check_steps > 0 and args.precision != "fp64":
+        ncheck = 2 * min(args.check_steps, mom.shape[1] // 2)
+        k64 = KPM(I.h1, I.eri, I.dipole, n, na, nb, precision="fp64")
+        t0 = time.perf_counter()
+        ref = k64.moments(psi0, comp, a, b, ncheck, check_bounds=False)
+        t64 = time.perf_counter() - t0
+        k64.close()
+        err = np.abs(mom[:, :ncheck] - ref) / np.abs(ref[:, :1])
+        acc = {"vs": "FP64 path (pinned to the oracle at 8o-12o and on sampled rows at 14o-18o)",
+               "nmoments": ncheck, "max_moment_err_over_omega0": float(err.max()),
+               "target": 1e-6, "fp64_seconds": round(t64, 2)}
+    moments_ok = bounded and (acc is None or acc["max_moment_err_over_omega0"] <= 1e-6)
 
     # roofline of the dominant kernel: the opposite-spin row pass (k_rowpass) on
     # the tensor-core paths, the gather kernel (the whole H application) otherwise
@@ -322,9 +385,10 @@ def run_ours(args, ws, rank, local, pg):
                      else "GB300 FP64 1.25 TFLOP/s")
         kname, share = "H application (k_sigma_gather)", sig_ms / ms
     achieved = flops / per_launch_s / 1e12
+    traffic, traffic_src = ncu_traffic(args.workload, args.precision)
     roof = {"bound": bound, "achieved": round(achieved, 4), "peak": round(peak, 2),
             "unit": "TFLOP/s", "frac": round(achieved / peak, 6),
-            "traffic": NCU_TRAFFIC_BYTES.get((args.workload, args.precision)),
+            "traffic": traffic, "traffic_source": traffic_src,
             "kernel": kname, "peak_source": peak_note,
             "algorithmic_flops_per_launch": flops,
             "launch_ms": round(per_launch_s * 1e3, 4), "launch_share": round(share, 4),
@@ -338,7 +402,7 @@ def run_ours(args, ws, rank, local, pg):
     pinned = torch.empty(dim, dtype=torch.float64, pin_memory=True)
     pinned.copy_(torch.from_numpy(psi0_host))
     pin_np = pinned.numpy()
-    nm_e2e = 2 * chunk * 2
+    nm_e2e = max(4, 2 * (args.e2e_moments // 2))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.e2e_requests):
@@ -358,20 +422,31 @@ def run_ours(args, ws, rank, local, pg):
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "fp16x(2,2)-f32acc",
                   "mixed_bf16": "bf16x2-f32acc"}[args.precision],
-        "data": "synthetic (seeded integrals, seeded normalised state in place of the NQS ground state)",
+        "data": ("synthetic (seeded integrals; psi0 = the GPU ground state of the same H in "
+                 "place of the NQS ground state)" if gs is not None else
+                 "synthetic (seeded integrals, seeded normalised state in place of the NQS "
+                 "ground state)"),
         "config": {"workload": args.workload, "norb": n, "nalpha": na, "nbeta": nb, "dim": dim,
                    "nmoments": w["nmoments"], "chebyshev_steps_per_bench_step": chunk,
                    "ncol": 1, "precision": args.precision, "parallelism": f"replicas{ws}",
                    "l2": "inputs larger than L2 (3 vectors of %.2f GB)" % (dim * k.vdtype.itemsize / 1e9),
-                   "a": a, "b": b},
+                   "timing": "CUDA events on the launching stream around the timed steps; "
+                             "per-launch events around each H application and row pass for "
+                             "the roofline, so the timed steps run as direct launches, not "
+                             "CUDA-graph replays",
+                   "a": a, "b": b, "ground_state": gs},
         "roofline": roof,
         "e2e": {"value": round(e2e_val, 4), "unit": UNIT, "h2d_bytes_per_step": dim * 8,
                 "d2h_bytes_per_step": nm_e2e * 8,
-                "note": f"kpm_moments_host, {nm_e2e} moments per request, psi0 from pinned host memory"},
+                "note": f"kpm_moments_host: {args.e2e_requests} request(s) of {nm_e2e} moments "
+                        f"({nm_e2e // 2} Chebyshev steps) each, psi0 copied from pinned host "
+                        f"memory and the moments read back inside the timed region; bytes are "
+                        f"per request"},
         "gpu_launches": int(launches),
         "tuned": dict(zip(("gemm_group_beta", "gemm_group_alpha"), k.tuned_params())),
         "clocks": clk,
         "moments_ok": moments_ok,
+        "accuracy": acc,
     }
     if cpu is not None:
         out["cpu_baseline"] = cpu
@@ -602,6 +677,67 @@ def run_accuracy(args):
     return out
 
 
+def run_convergence(args):
+    """Resolution of the spectrum vs the number of moments N (the synthetic analogue
+    of the paper's convergence study, Results "Resolution of absorption spectra",
+    with its N_Omega = 400 |e_g| heuristic marked).  Ground state from
+    kpm_ground_state on an FP64 context; the moments of the z component up to NMAX
+    from one deflated recursion in --precision and one in FP64 (the reference, pinned
+    to the oracle); for every N: the relative L2 error of the --precision spectrum
+    against the FP64 one, the distance to the NMAX spectrum, and the number of peaks
+    resolved above 1 % of the maximum."""
+    import torch
+
+    from paper_2506_07430_gb300 import KPM, spectrum
+
+    torch.cuda.set_device(0)
+    w = synthetic.workload(args.workload)
+    n, na, nb = w["norb"], w["nalpha"], w["nbeta"]
+    I = synthetic.integrals(n, na, nb, w["seed"])
+    nmax = int(args.convergence)
+    k64 = KPM(I.h1, I.eri, I.dipole, n, na, nb, precision="fp64")
+    t0 = time.perf_counter()
+    e0, res, psi = k64.ground_state(iters=60, max_cycles=30, tol=1e-10)
+    t_gs = time.perf_counter() - t0
+    emin, emax = k64.bounds(iters=200, seed=2506001)
+    a, b = KPM.scale(emin, emax)
+    t0 = time.perf_counter()
+    ref = k64.moments_deflated(psi, e0, 0b100, a, b, nmax)[0]
+    t64 = time.perf_counter() - t0
+    k64.close()
+    kp = KPM(I.h1, I.eri, I.dipole, n, na, nb, precision=args.precision)
+    t0 = time.perf_counter()
+    mom = kp.moments_deflated(psi, e0, 0b100, a, b, nmax)[0]
+    tp = time.perf_counter() - t0
+    kp.close()
+    M = 4096
+    Ns = []
+    N = 256
+    while N <= nmax:
+        Ns.append(N)
+        N *= 2
+    top = spectrum(mom, a, b, M)[1]
+    rows = []
+    for N in Ns:
+        om, it = spectrum(mom[:N], a, b, M)
+        _, it64 = spectrum(ref[:N], a, b, M)
+        inner = (it[1:-1] > it[:-2]) & (it[1:-1] > it[2:]) & (it[1:-1] > 1e-2 * it.max())
+        rows.append({"N": N,
+                     "spectrum_rel_l2_vs_fp64": float(np.linalg.norm(it - it64) / np.linalg.norm(it64)),
+                     "moment_err_over_omega0": float(np.abs(mom[:N] - ref[:N]).max() / abs(ref[0])),
+                     "rel_l2_to_nmax": float(np.linalg.norm(it - top) / np.linalg.norm(top)),
+                     "peaks": int(inner.sum()),
+                     "resolution_hartree": float(np.pi * a / N)})
+    return {"metric": "spectrum convergence with the number of moments",
+            "config": {"workload": args.workload, "precision": args.precision, "component": "z",
+                       "state": "GPU ground state (kpm_ground_state, FP64)", "e0": e0,
+                       "ground_state_residual": res, "a": a, "b": b, "npoints": M,
+                       "N_Omega_400_abs_e0": int(round(400 * abs(e0)))},
+            "seconds": {"ground_state": round(t_gs, 2), "fp64_moments": round(t64, 2),
+                        args.precision + "_moments": round(tp, 2)},
+            "rows": rows}
+
+
 def _percentile(xs, q):
     xs = sorted(xs)
     if not xs:
@@ -726,6 +862,9 @@ def main():
         return
     if args.accuracy:
         print(json.dumps(run_accuracy(args)), flush=True)
+        return
+    if args.convergence:
+        print(json.dumps(run_convergence(args)), flush=True)
         return
     if args.graphs_compare:
         print(json.dumps(run_graphs_compare(args)), flush=True)

@@ -69,13 +69,18 @@ typedef enum {
     KPM_FP64 = 0,      /* FP64 vectors and arithmetic everywhere (reference path)     */
     KPM_FP32 = 1,      /* FP32 vectors, FP32 CUDA-core sigma with the diagonal H_II
                           evaluated in FP64; FP64 dots/moments                        */
-    KPM_MIXED = 2,     /* FP32 vectors; two-electron sigma on tensor cores (tcgen05):
-                          operands split into FP16 pieces with power-of-two scaling
-                          (x in 2, integrals in 3 pieces, 4 MMAs, FP32 accumulation);
-                          FP64 dots/moments; up to 16 orbitals                       */
+    KPM_MIXED = 2,     /* FP32 vectors; the opposite-spin two-electron term and the
+                          same-spin string Hamiltonians on tensor cores (tcgen05):
+                          x and the integrals each split into 2 FP16 pieces with
+                          power-of-two scales, 3 MMAs per product (hi*hi, lo*hi,
+                          hi*lo), FP32 accumulation; same-spin diagonals added
+                          exactly; FP64 dots/moments; up to 16 orbitals               */
     KPM_MIXED_BF16 = 3 /* as KPM_MIXED with split-BF16 operands (2 pieces each,
                           3 MMAs): ~16 significant bits per product                  */
 } kpm_precision;
+
+/* Parameter lambda of the Lorentz kernel (kernel = 2) of kpm_spectrum. */
+#define KPM_LORENTZ_LAMBDA 4.0
 
 /* Largest orbital count this build supports (strings are 32-bit masks, string
  * ranks are 16-bit in packed tables: C(18,9) = 48620 < 65536). */
@@ -132,8 +137,10 @@ kpm_status kpm_string_table(const kpm_ctx* ctx, int spin, uint32_t* masks, int32
 /*
  * kpm_sigma -- y = H x for ncol columns (device, [ncol][dim], x and y distinct).
  * Queued on the context's stream (asynchronous).  FP64: plain gathers in FP64;
- * FP32: FP32 gathers; MIXED: tensor-core two-electron terms (split-BF16 operands,
- * FP32 accumulation) plus FP32 gathers.
+ * FP32: FP32 gathers with the diagonal H_II evaluated in FP64; KPM_MIXED /
+ * KPM_MIXED_BF16: the opposite-spin term and the same-spin products on tensor
+ * cores (split FP16 / BF16 operands, FP32 accumulation), the same-spin
+ * diagonals added exactly.
  * Paper: Methods, second-quantized Hamiltonian.
  */
 kpm_status kpm_sigma(kpm_ctx* ctx, const void* x, void* y, int ncol);
@@ -155,6 +162,31 @@ kpm_status kpm_apply_dipole(kpm_ctx* ctx, int comp, const double* psi_dev, void*
  */
 kpm_status kpm_bounds(kpm_ctx* ctx, int iters, uint64_t seed, double* emin, double* emax);
 
+/*
+ * kpm_ground_state -- the lowest eigenpair of H, the |0> that the dipole
+ * recursion starts from (the paper obtains |0> from its NQS; here it is found
+ * on the GPU with the library's own sigma).  Explicitly restarted Lanczos: each
+ * cycle runs `iters` Lanczos steps (FP64 dots and tridiagonal, vectors in the
+ * context precision) from the current start vector, takes the lowest Ritz pair
+ * of the tridiagonal (Sturm bisection and inverse iteration on the device),
+ * regenerates the same Lanczos vectors in a second pass to form the Ritz
+ * vector psi = sum_j s_j v_j in FP64, normalises it, and restarts from it,
+ * until |H psi - E psi| <= tol or max_cycles cycles have run.  The first start
+ * vector is drawn with the SplitMix64 counter generator seeded by `seed`.
+ *   psi_dev  FP64 device [dim] (caller-owned), out: the unit Ritz vector
+ *            (overall sign arbitrary; moments do not depend on it).
+ *   e0       host out: E = <psi|H|psi> (H applied in the context precision).
+ *   resid    host out: |H psi - E psi| of the last cycle (2-norm, energy units);
+ *            above tol if max_cycles ran out (the call still returns KPM_OK).
+ * Each cycle costs 2 iters + 1 H applications.  Synchronous.  Errors:
+ * KPM_EINVAL (iters outside 2..4096, max_cycles outside 1..10000, tol <= 0, NULL
+ * pointers), KPM_ETIMEOUT / KPM_ECUDA as kpm_synchronize.
+ * Paper: Methods, "KPM for absorption spectra" (|alpha> = mu|0> from the ground
+ * state |0>); Results, absorption spectra (Lanczos for the FCI baselines).
+ */
+kpm_status kpm_ground_state(kpm_ctx* ctx, int iters, int max_cycles, double tol, uint64_t seed,
+                            double* psi_dev, double* e0, double* resid);
+
 /* a = (emax - emin) / (2 - eps), b = (emax + emin) / 2. */
 void kpm_scale(double emin, double emax, double eps, double* a, double* b);
 
@@ -174,6 +206,29 @@ kpm_status kpm_moments(kpm_ctx* ctx, const double* psi0_dev, unsigned comp_mask,
 /* As kpm_moments with psi0 in host memory (copied to the device inside). */
 kpm_status kpm_moments_host(kpm_ctx* ctx, const double* psi0_host, unsigned comp_mask,
                             double a, double b, int nmoments, double* moments_host);
+
+/*
+ * kpm_moments_deflated -- kpm_moments for a ground state psi0 that is an
+ * eigenvector of H with eigenvalue e0, known to FP64 accuracy (for example
+ * from kpm_ground_state on a KPM_FP64 context).  The same moments (Eq.
+ * moments), evaluated with less round-off: alpha_0 = mu psi0 splits into
+ * c0 p + alpha_perp with p = psi0/|psi0| and c0 = <p|alpha_0> (FP64), and since
+ * T_n(H~) p = T_n(x0) p, x0 = (e0 - b)/a,
+ *   Omega_n = c0^2 T_n(x0) + <alpha_perp|T_n(H~)|alpha_perp>.
+ * The recursion (context precision) runs on alpha_perp only; the permanent-
+ * dipole term c0^2 T_n(x0) (the peak at omega = e0) is added in FP64 in closed
+ * form.  With FP32 vectors this removes the error that grows linearly with n
+ * from the ground-state component at the edge of the spectrum, where the
+ * Chebyshev recursion amplifies round-off most.  If psi0 is not an eigenvector
+ * the cross terms c0 <p|T_n(H~)|alpha_perp> are dropped: results are then only
+ * as accurate as psi0's residual |H psi0 - e0 psi0| allows.
+ * Arguments and errors as kpm_moments; KPM_EINVAL also if e0 lies outside
+ * [b - a, b + a].  Paper: Eq. moments; Methods, KPM for absorption spectra
+ * (|alpha> = mu|0> with |0> the ground state).
+ */
+kpm_status kpm_moments_deflated(kpm_ctx* ctx, const double* psi0_dev, double e0,
+                                unsigned comp_mask, double a, double b, int nmoments,
+                                double* moments_host);
 
 /*
  * kpm_moments_batch -- kpm_moments for `count` molecules at once: after each
@@ -210,6 +265,10 @@ kpm_status kpm_moments_batch(kpm_ctx* const* ctxs, int count, const double* cons
  */
 kpm_status kpm_recursion_begin(kpm_ctx* ctx, const double* psi0_dev, unsigned comp_mask,
                                double a, double b, int max_moments);
+/* kpm_recursion_begin with the ground-state deflation of kpm_moments_deflated. */
+kpm_status kpm_recursion_begin_deflated(kpm_ctx* ctx, const double* psi0_dev, double e0,
+                                        unsigned comp_mask, double a, double b,
+                                        int max_moments);
 kpm_status kpm_recursion_advance(kpm_ctx* ctx, int nsteps);
 kpm_status kpm_recursion_moments(kpm_ctx* ctx, double* moments_host, int* nmoments_out);
 
@@ -227,12 +286,14 @@ kpm_status kpm_recursion_moments(kpm_ctx* ctx, double* moments_host, int* nmomen
 kpm_status kpm_recursion_advance_batch(kpm_ctx* const* ctxs, int count, int nsteps);
 
 /*
- * kpm_spectrum -- Jackson-damped (kernel=1) or undamped (kernel=0) Chebyshev
- * reconstruction on the npoints Chebyshev nodes x_k = cos(pi (k+1/2)/M):
+ * kpm_spectrum -- Jackson-damped (kernel=1), Lorentz-damped (kernel=2, lambda =
+ * KPM_LORENTZ_LAMBDA) or undamped (kernel=0) Chebyshev reconstruction on the
+ * npoints Chebyshev nodes x_k = cos(pi (k+1/2)/M):
  *   I(x) = (g_0 Omega_0 + 2 sum_{n>=1} g_n Omega_n T_n(x)) / (pi sqrt(1-x^2)),
  *   omega = a x + b, intensity = I(x) / a (density per unit energy),
  * written in ascending omega.  g_n = [(N-n+1) cos(pi n/(N+1)) +
- * sin(pi n/(N+1)) cot(pi/(N+1))]/(N+1), n = 0..N-1.  moments, omega_out,
+ * sin(pi n/(N+1)) cot(pi/(N+1))]/(N+1), n = 0..N-1 (Jackson); g_n =
+ * sinh(lambda (1 - n/N)) / sinh(lambda) (Lorentz).  moments, omega_out,
  * intensity_out are host arrays; the sums run in a CUDA kernel on the current
  * device's legacy stream.  Synchronous.  No context needed.
  * Paper: Eq. kpm, Eq. jackson (with the (N-n+1) factor of the KPM review the
@@ -240,6 +301,35 @@ kpm_status kpm_recursion_advance_batch(kpm_ctx* const* ctxs, int count, int nste
  */
 kpm_status kpm_spectrum(const double* moments, int nmoments, double a, double b,
                         int npoints, int kernel, double* omega_out, double* intensity_out);
+
+/*
+ * kpm_spectrum_lorentz -- kpm_spectrum with the Lorentz kernel g_n =
+ * sinh(lambda (1 - n/N)) / sinh(lambda), lambda > 0 chosen by the caller (the
+ * KPM review the paper cites recommends 3..5; the broadening is about lambda/N
+ * in x).  Paper: Methods, "modified kernels like the Jackson kernel".
+ */
+kpm_status kpm_spectrum_lorentz(const double* moments, int nmoments, double a, double b,
+                                int npoints, double lambda, double* omega_out,
+                                double* intensity_out);
+
+/*
+ * kpm_moments_cross -- moments of the dynamical correlation function of two
+ * one-body operators (Methods, C_AB): Omega_n = <0| A T_n(H~) B |0>, n < N,
+ * with A = sum_pq op_a[p][q] E_pq and B = sum_pq op_b[p][q] E_pq (spin-summed,
+ * real symmetric n x n host matrices; the dipole component c is op = -d^c).
+ * Two recursions run as one block, a_n = T_n(H~) A|0> and b_n = T_n(H~) B|0>,
+ * and since T_m T_n = (T_{m+n} + T_{|m-n|})/2 for the symmetric H~,
+ *   Omega_2n = 2 <a_n|b_n> - Omega_0,  Omega_2n+1 = 2 <a_n+1|b_n> - Omega_1
+ * (FP64 cross dots), N/2 steps of two columns.  A = B reproduces kpm_moments.
+ *   psi0_dev       FP64 device [dim], the ground state.
+ *   moments_host   host [nmoments], nmoments even and >= 2.
+ * Synchronous.  Errors: KPM_EINVAL (NULL, nmoments, a, b, non-symmetric op),
+ * KPM_EBOUNDS if some |Omega_n| exceeds sqrt(<0|A^2|0> <0|B^2|0>) (1 + 1e-6)
+ * (the Cauchy-Schwarz bound; moments still written).
+ */
+kpm_status kpm_moments_cross(kpm_ctx* ctx, const double* psi0_dev, const double* op_a,
+                             const double* op_b, double a, double b, int nmoments,
+                             double* moments_host);
 
 /*
  * kpm_synchronize -- waits for all work queued on the context's stream and
@@ -295,7 +385,22 @@ kpm_status kpm_profile_read(kpm_ctx* ctx, double* sigma_ms, int* count);
 kpm_status kpm_profile_read_rowpass(kpm_ctx* ctx, double* rowpass_ms, int* count);
 
 /*
- * kpm_spectrum_static -- kpm_spectrum for callers that cannot allocate device
+ * kpm_test_rowpass_stall -- testing aid for the bounded waits of the
+ * tensor-core row pass (KPM_MIXED / KPM_MIXED_BF16 contexts).  With enable != 0
+ * the next row pass (the first column of the next H application) issues no
+ * MMAs, so the mbarrier waits of its copy and scatter warps run out after about
+ * 10 ms instead of the normal ~2 s limit; the kernel records the expiry, waits
+ * for its own copies in flight, frees its tensor memory and returns with its
+ * rows unwritten.  kpm_synchronize then reports KPM_ETIMEOUT and clears the
+ * flag; the context stays usable and later H applications are exact again.
+ * Nothing faults and nothing waits without a limit.  The paper has no
+ * counterpart (this library's failure detection).  Errors: KPM_EINVAL for a NULL
+ * or non-tensor-core context.
+ */
+kpm_status kpm_test_rowpass_stall(kpm_ctx* ctx, int enable);
+
+/*
+ * kpm_spectrum_static -- kpm_spectrum (kernels 0, 1, 2) for callers that cannot allocate device
  * memory.  The paper has no counterpart; this entry point exists for callers
  * that cannot call cudaMalloc: processes whose device memory is entirely
  * reserved by another allocator (a framework's caching pool, a fixed memory
@@ -310,7 +415,9 @@ kpm_status kpm_profile_read_rowpass(kpm_ctx* ctx, double* rowpass_ms, int* count
  * memory, held by every GPU that loads the library until the process exits.
  * nmoments above that limit is rejected with KPM_EINVAL.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) and caches
- * it; make that first call before any stream capture.  Every call on a device
+ * it for the life of the process; make that first call before any stream
+ * capture, and do not call it again on a device after cudaDeviceReset (the
+ * cached address belonged to the destroyed context).  Every call on a device
  * shares the one array, so calls whose work overlaps on the GPU (for example
  * on two streams at once) race and give undefined results; serialise them.
  * The array needs no clearing: every element read is written first in stream
@@ -334,7 +441,10 @@ kpm_status kpm_spectrum_static(const double* moments_dev, int nmoments, double a
  * reconstructs the spectrum (Jackson kernel optional) of the moments summed
  * over the requested dipole components and frees the request's memory.
  * A request computes with the same kernels whether it runs alone or beside
- * others, so its result is the same.
+ * others, so its result is the same.  Set-up (kpm_create, the dipole and the
+ * first step) runs on a second thread, overlapping the rounds of the resident
+ * requests.  A request whose set-up or advance fails is finished at once with
+ * that status, and its slot and budget are released.
  */
 typedef struct kpm_server kpm_server;
 
@@ -355,7 +465,9 @@ typedef struct {
     double a, b;           /* rescaling H~ = (H - b)/a (e.g. from kpm_bounds)      */
     int nmoments;          /* even, >= 2                                           */
     int npoints;           /* Chebyshev nodes of the spectrum                      */
-    int kernel;            /* 1 = Jackson, 0 = none                                */
+    int kernel;            /* 1 = Jackson, 2 = Lorentz (KPM_LORENTZ_LAMBDA), 0 = none */
+    int deflate;           /* 1: psi0 is an eigenvector of energy e0, use the      */
+    double e0;             /*    deflated recursion of kpm_moments_deflated        */
 } kpm_request;
 
 typedef struct {
@@ -381,8 +493,18 @@ kpm_status kpm_server_wait(kpm_server* s, uint64_t id, int timeout_ms, kpm_resul
 kpm_status kpm_server_cancel(kpm_server* s, uint64_t id);
 /* Device memory held by admitted requests, resident and queued counts. */
 kpm_status kpm_server_stats(kpm_server* s, size_t* mem_used, int* resident, int* queued);
-/* Cancels what is queued, finishes nothing further, joins the worker. */
+/* Cancels what is queued, lets the resident requests (and one being set up)
+ * run to their end, then joins the server's threads. */
 void kpm_server_destroy(kpm_server* s);
+
+/* Testing aid for the server's failure handling (host-side fault injection;
+ * no GPU work faults): the next round that would advance request id treats
+ * that advance as having returned `status` (not KPM_OK).  The request is then
+ * finished with that status (kpm_server_wait returns it), its slot and budget
+ * are released, and the other requests go on unchanged.  The paper has no
+ * counterpart.  Errors: KPM_EINVAL for a NULL server, KPM_OK as status, or an
+ * unknown (or already collected) id. */
+kpm_status kpm_server_inject_failure(kpm_server* s, uint64_t id, kpm_status status);
 
 /* Number of kernels this library launched on the calling process so far. */
 uint64_t kpm_launch_count(void);

@@ -33,8 +33,8 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["jackson", "moments_recursion", "moments_recursion_block", "moments_direct",
-           "moments_eigen",
+__all__ = ["jackson", "lorentz", "moments_recursion", "moments_recursion_block",
+           "moments_direct", "moments_cross", "moments_cross_eigen", "moments_eigen",
            "chebyshev_nodes", "spectrum", "spectrum_eigen", "scale_from_bounds"]
 
 
@@ -43,6 +43,14 @@ def jackson(N: int) -> np.ndarray:
     n = np.arange(N, dtype=np.float64)
     q = np.pi / (N + 1)
     return ((N - n + 1) * np.cos(q * n) + np.sin(q * n) / np.tan(q)) / (N + 1)
+
+
+def lorentz(N: int, lam: float = 4.0) -> np.ndarray:
+    """Lorentz damping factors g_n = sinh(lam (1 - n/N)) / sinh(lam), n = 0 .. N-1
+    (the KPM review cited in Methods; the paper names modified kernels "like the
+    Jackson kernel")."""
+    n = np.arange(N, dtype=np.float64)
+    return np.sinh(lam * (1.0 - n / N)) / np.sinh(lam)
 
 
 def scale_from_bounds(emin: float, emax: float, eps: float = 0.01):
@@ -116,6 +124,33 @@ def moments_direct(apply_h, alpha0, a, b, nmoments):
     return out
 
 
+def moments_cross(apply_h, left: np.ndarray, right: np.ndarray, a: float, b: float,
+                  nmoments: int):
+    """Omega_n = <left|T_n(H~)|right> (Methods: C_AB moments <0|A T_n(H~) B|0> with
+    left = A^dagger|0>, right = B|0>), one H product per moment, no doubling."""
+    l = np.asarray(left, np.float64)
+    prev = np.asarray(right, np.float64)
+    out = np.empty(nmoments)
+    out[0] = l @ prev
+    if nmoments == 1:
+        return out
+    cur = (apply_h(prev) - b * prev) / a
+    out[1] = l @ cur
+    for n in range(2, nmoments):
+        nxt = 2.0 * (apply_h(cur) - b * cur) / a - prev
+        out[n] = l @ nxt
+        prev, cur = cur, nxt
+    return out
+
+
+def moments_cross_eigen(evals, U, left, right, a, b, nmoments):
+    """Omega_n = sum_k <left|k><k|right> T_n(E~_k) from eigenpairs (columns of U)."""
+    x = (np.asarray(evals) - b) / a
+    w = (U.T @ np.asarray(left)) * (U.T @ np.asarray(right))
+    n = np.arange(nmoments)
+    return (np.cos(np.outer(n, np.arccos(x))) * w[None, :]).sum(axis=1)
+
+
 def moments_eigen(evals: np.ndarray, weights: np.ndarray, a: float, b: float, nmoments: int):
     """Omega_n = sum_k w_k T_n(E~_k), T_n(x) = cos(n arccos x) (Eq. moments in the eigenbasis)."""
     x = (np.asarray(evals) - b) / a
@@ -132,15 +167,22 @@ def chebyshev_nodes(M: int) -> np.ndarray:
     return np.cos(np.pi * (k + 0.5) / M)
 
 
-def spectrum(moments: np.ndarray, a: float, b: float, npoints: int, kernel: str = "jackson"):
-    """(omega ascending, density in energy units) by a direct cosine sum.
+def spectrum(moments: np.ndarray, a: float, b: float, npoints: int, kernel: str = "jackson",
+             lam: float = 4.0):
+    """(omega ascending, density in energy units) by a direct cosine sum; kernel
+    "jackson", "lorentz" (parameter lam) or "none".
 
     I(x_k) = (g_0 Omega_0 + 2 sum_{n>=1} g_n Omega_n cos(n theta_k)) / (pi sin theta_k),
     theta_k = pi (k + 1/2) / M, omega_k = a x_k + b, density = I / a.
     """
     mu = np.asarray(moments, np.float64)
     N = len(mu)
-    g = jackson(N) if kernel == "jackson" else np.ones(N)
+    if kernel == "jackson":
+        g = jackson(N)
+    elif kernel == "lorentz":
+        g = lorentz(N, lam)
+    else:
+        g = np.ones(N)
     mt = g * mu
     k = np.arange(npoints, dtype=np.float64)
     th = np.pi * (k + 0.5) / npoints

@@ -31,20 +31,26 @@ SIGNATURES = {
     "kpm_apply_dipole": (_I, [_P, _I, _P, _P]),
     "kpm_bounds": (_I, [_P, _I, _U64, _P, _P]),
     "kpm_scale": (None, [_D, _D, _D, _P, _P]),
+    "kpm_ground_state": (_I, [_P, _I, _I, _D, _U64, _P, _P, _P]),
     "kpm_moments": (_I, [_P, _P, _U, _D, _D, _I, _P]),
     "kpm_moments_host": (_I, [_P, _P, _U, _D, _D, _I, _P]),
     "kpm_moments_batch": (_I, [_P, _I, _P, _U, _P, _P, _I, _P]),
+    "kpm_moments_deflated": (_I, [_P, _P, _D, _U, _D, _D, _I, _P]),
+    "kpm_recursion_begin_deflated": (_I, [_P, _P, _D, _U, _D, _D, _I]),
     "kpm_recursion_begin": (_I, [_P, _P, _U, _D, _D, _I]),
     "kpm_recursion_advance": (_I, [_P, _I]),
     "kpm_recursion_advance_batch": (_I, [_P, _I, _I]),
     "kpm_recursion_moments": (_I, [_P, _P, _P]),
     "kpm_spectrum": (_I, [_P, _I, _D, _D, _I, _I, _P, _P]),
+    "kpm_spectrum_lorentz": (_I, [_P, _I, _D, _D, _I, _D, _P, _P]),
+    "kpm_moments_cross": (_I, [_P, _P, _P, _P, _D, _D, _I, _P]),
     "kpm_synchronize": (_I, [_P]),
     "kpm_profile_enable": (_I, [_P, _I]),
     "kpm_profile_read": (_I, [_P, _P, _P]),
     "kpm_profile_read_rowpass": (_I, [_P, _P, _P]),
     "kpm_graphs_enable": (_I, [_P, _I]),
     "kpm_tuned_params": (_I, [_P, _P, _P]),
+    "kpm_test_rowpass_stall": (_I, [_P, _I]),
     "kpm_spectrum_static": (_I, [_P, _I, _D, _D, _I, _I, _P, _P, _P]),
     "kpm_server_create": (_I, [_P, _P]),
     "kpm_server_submit": (_I, [_P, _P, _P]),
@@ -52,6 +58,7 @@ SIGNATURES = {
     "kpm_server_cancel": (_I, [_P, _U64]),
     "kpm_server_stats": (_I, [_P, _P, _P, _P]),
     "kpm_server_destroy": (None, [_P]),
+    "kpm_server_inject_failure": (_I, [_P, _U64, _I]),
     "kpm_launch_count": (_U64, []),
 }
 
@@ -64,7 +71,7 @@ class ServerConfig(ctypes.Structure):
 class Request(ctypes.Structure):
     _fields_ = [("h1", _P), ("eri", _P), ("dipole", _P), ("norb", _I), ("nalpha", _I),
                 ("nbeta", _I), ("psi0", _P), ("comp_mask", _U), ("a", _D), ("b", _D),
-                ("nmoments", _I), ("npoints", _I), ("kernel", _I)]
+                ("nmoments", _I), ("npoints", _I), ("kernel", _I), ("deflate", _I), ("e0", _D)]
 
 
 class Result(ctypes.Structure):
@@ -206,6 +213,18 @@ class KPM:
                self._h)
         return lo.value, hi.value
 
+    def ground_state(self, iters: int = 60, max_cycles: int = 20, tol: float = 1e-9,
+                     seed: int = 2506002, out=None):
+        """(E0, residual, psi) with psi a CUDA float64 tensor (kpm_ground_state)."""
+        import torch
+        if out is None:
+            out = torch.empty(self.dim, dtype=torch.float64, device="cuda")
+        e0, res = ctypes.c_double(), ctypes.c_double()
+        _check(self._lib().kpm_ground_state(self._h, iters, max_cycles, tol, seed,
+                                            _dev_ptr(out, torch.float64), ctypes.byref(e0),
+                                            ctypes.byref(res)), self._h)
+        return e0.value, res.value, out
+
     @staticmethod
     def scale(emin: float, emax: float, eps: float = 0.01):
         a, b = ctypes.c_double(), ctypes.c_double()
@@ -230,12 +249,49 @@ class KPM:
         _check(st, self._h)
         return out
 
-    def recursion_begin(self, psi0, comp_mask: int, a: float, b: float, max_moments: int):
+    def moments_deflated(self, psi0, e0: float, comp_mask: int, a: float, b: float,
+                         nmoments: int, check_bounds: bool = True):
+        """Moments [ncomp, nmoments] for an eigenvector psi0 (CUDA float64) of energy e0,
+        with the ground-state term in closed form (kpm_moments_deflated)."""
+        import torch
+        ncomp = bin(comp_mask).count("1")
+        out = np.zeros((ncomp, nmoments), np.float64)
+        st = self._lib().kpm_moments_deflated(self._h, _dev_ptr(psi0, torch.float64), e0,
+                                              comp_mask, a, b, nmoments, _np_ptr(out))
+        if st == KPM_EBOUNDS and not check_bounds:
+            return out
+        _check(st, self._h)
+        return out
+
+    def moments_cross(self, psi0, op_a, op_b, a: float, b: float, nmoments: int,
+                      check_bounds: bool = True):
+        """Omega_n = <0|A T_n(H~) B|0> for one-body A = sum op_a E, B = sum op_b E
+        (symmetric n x n host matrices) (kpm_moments_cross)."""
+        import torch
+        n = self.norb
+        oa = np.ascontiguousarray(op_a, dtype=np.float64).reshape(n, n)
+        ob = np.ascontiguousarray(op_b, dtype=np.float64).reshape(n, n)
+        out = np.zeros(nmoments, np.float64)
+        st = self._lib().kpm_moments_cross(self._h, _dev_ptr(psi0, torch.float64), _np_ptr(oa),
+                                           _np_ptr(ob), a, b, nmoments, _np_ptr(out))
+        if st == KPM_EBOUNDS and not check_bounds:
+            return out
+        _check(st, self._h)
+        return out
+
+    def recursion_begin(self, psi0, comp_mask: int, a: float, b: float, max_moments: int,
+                        e0: float | None = None):
+        """Start a resumable recursion; with e0, the deflated form (psi0 an eigenvector)."""
         import torch
         self._rec_ncomp = bin(comp_mask).count("1")
         self._rec_max = max_moments
-        _check(self._lib().kpm_recursion_begin(self._h, _dev_ptr(psi0, torch.float64), comp_mask,
-                                               a, b, max_moments), self._h)
+        if e0 is None:
+            st = self._lib().kpm_recursion_begin(self._h, _dev_ptr(psi0, torch.float64),
+                                                 comp_mask, a, b, max_moments)
+        else:
+            st = self._lib().kpm_recursion_begin_deflated(self._h, _dev_ptr(psi0, torch.float64),
+                                                          e0, comp_mask, a, b, max_moments)
+        _check(st, self._h)
 
     def recursion_advance(self, nsteps: int):
         _check(self._lib().kpm_recursion_advance(self._h, nsteps), self._h)
@@ -248,6 +304,11 @@ class KPM:
         gb, ga = ctypes.c_int(), ctypes.c_int()
         _check(self._lib().kpm_tuned_params(self._h, ctypes.byref(gb), ctypes.byref(ga)), self._h)
         return gb.value, ga.value
+
+    def test_rowpass_stall(self, on: bool = True):
+        """Testing aid: the next tensor-core row pass stalls until its bounded waits
+        run out (kpm_test_rowpass_stall)."""
+        _check(self._lib().kpm_test_rowpass_stall(self._h, 1 if on else 0), self._h)
 
     def graphs_enable(self, on: bool = True):
         _check(self._lib().kpm_graphs_enable(self._h, 1 if on else 0), self._h)
@@ -292,14 +353,17 @@ class Server:
         self._pending = {}
 
     def submit(self, h1, eri, dipole, norb, nalpha, nbeta, psi0, comp_mask, a, b, nmoments,
-               npoints=2048, kernel="jackson"):
+               npoints=2048, kernel="jackson", e0=None):
+        """Queue a request; with e0 (psi0 an eigenvector of that energy) the recursion
+        runs deflated (kpm_moments_deflated)."""
         keep = [np.ascontiguousarray(h1, dtype=np.float64),
                 np.ascontiguousarray(eri, dtype=np.float64),
                 np.ascontiguousarray(dipole, dtype=np.float64),
                 np.ascontiguousarray(psi0, dtype=np.float64)]
         r = Request(_np_ptr(keep[0]), _np_ptr(keep[1]), _np_ptr(keep[2]), norb, nalpha, nbeta,
                     _np_ptr(keep[3]), comp_mask, a, b, nmoments, npoints,
-                    1 if kernel == "jackson" else 0)
+                    KERNELS[kernel], 0 if e0 is None else 1,
+                    0.0 if e0 is None else float(e0))
         rid = ctypes.c_uint64()
         _check(load_library().kpm_server_submit(self._h, ctypes.byref(r), ctypes.byref(rid)), None)
         self._pending[rid.value] = (bin(comp_mask).count("1"), nmoments, npoints)
@@ -319,6 +383,10 @@ class Server:
             _check(st, None)
         return {"moments": mom, "omega": om, "intensity": it, "t_queue_s": res.t_queue_s,
                 "t_run_s": res.t_run_s, "t_total_s": res.t_total_s, "status": st}
+
+    def inject_failure(self, rid: int, status: int):
+        """Testing aid: the next advance of request rid fails with `status`."""
+        _check(load_library().kpm_server_inject_failure(self._h, rid, status), None)
 
     def cancel(self, rid: int):
         _check(load_library().kpm_server_cancel(self._h, rid), None)
@@ -374,13 +442,22 @@ def recursion_advance_batch(kpms, nsteps: int):
     _check(load_library().kpm_recursion_advance_batch(ctxs, count, nsteps), kpms[0]._h)
 
 
-def spectrum(moments, a: float, b: float, npoints: int = 2048, kernel: str = "jackson"):
-    """(omega ascending, intensity per unit energy) on the Chebyshev nodes."""
+KERNELS = {"none": 0, "jackson": 1, "lorentz": 2}
+
+
+def spectrum(moments, a: float, b: float, npoints: int = 2048, kernel: str = "jackson",
+             lam: float | None = None):
+    """(omega ascending, intensity per unit energy) on the Chebyshev nodes; kernel
+    "jackson", "lorentz" (parameter lam, default KPM_LORENTZ_LAMBDA) or "none"."""
     lib = load_library()
     mu = np.ascontiguousarray(moments, dtype=np.float64).reshape(-1)
     om = np.zeros(npoints, np.float64)
     it = np.zeros(npoints, np.float64)
-    st = lib.kpm_spectrum(_np_ptr(mu), len(mu), a, b, npoints, 1 if kernel == "jackson" else 0,
-                          _np_ptr(om), _np_ptr(it))
+    if kernel == "lorentz" and lam is not None:
+        st = lib.kpm_spectrum_lorentz(_np_ptr(mu), len(mu), a, b, npoints, float(lam),
+                                      _np_ptr(om), _np_ptr(it))
+    else:
+        st = lib.kpm_spectrum(_np_ptr(mu), len(mu), a, b, npoints, KERNELS[kernel],
+                              _np_ptr(om), _np_ptr(it))
     _check(st, None)
     return om, it

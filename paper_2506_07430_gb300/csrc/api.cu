@@ -36,9 +36,15 @@ struct kpm_ctx {
     DevBuf vA, vB, vS, dots, moments_dev, partials, counters, psi_tmp;
     void* rec_prev = nullptr;
     void* rec_cur = nullptr;
+    // deflated recursion (kpm_recursion_begin_deflated): per column the weight c0^2
+    // of the ground state in alpha_0 and x0 = (e0 - b)/a; FP64 scratch vectors
+    bool rec_deflated = false;
+    double rec_x0 = 0.0;
+    DevBuf dfl_c, dfl_p, dfl_a;
+    DevBuf x_ops, x_cross;            // kpm_moments_cross: operator integrals, cross dots
 
-    // Lanczos state
-    DevBuf lz_v0, lz_v1, lz_w, lz_ab, lz_scalar;
+    // Lanczos state (spectral bounds, ground state)
+    DevBuf lz_v0, lz_v1, lz_w, lz_ab, lz_scalar, lz_start;
 
     // profiling of H applications
     bool prof = false;
@@ -219,7 +225,71 @@ void rec_begin(kpm_ctx* c, const double* psi0, unsigned mask, double a, double b
     c->rec_prev = c->vB.p;  // alpha_0
     c->rec_cur = c->vA.p;   // alpha_1
     c->rec_steps = 1;
+    c->rec_deflated = false;
     // buffers may have moved: captured steps are stale
+    c->drop_graphs();
+    c->step_ctr.ensure(sizeof(unsigned));
+    step_set(c->step_ctr.as<unsigned>(), 1u, c->st);
+}
+
+// As rec_begin for a ground state psi0 with eigenvalue e0: alpha_0 = mu psi0 is
+// split into c0 p + alpha_perp (p = psi0 / |psi0|, c0 = <p|alpha_0>, all in FP64,
+// alpha_perp then stored in the context precision)
+// and the recursion runs on alpha_perp; the collected moments add c0^2 T_n(x0),
+// x0 = (e0 - b)/a, which is <c0 p|T_n(H~)|c0 p> for an eigenvector (the cross
+// terms vanish since T_n(H~) p = T_n(x0) p is orthogonal to alpha_perp).
+void rec_begin_deflated(kpm_ctx* c, const double* psi0, double e0, unsigned mask, double a,
+                        double b, int max_moments) {
+    if (!psi0) KPM_THROW(KPM_EINVAL, "psi0 is NULL");
+    if ((mask & ~7u) || !mask) KPM_THROW(KPM_EINVAL, "comp_mask must be a non-empty subset of {1,2,4}");
+    if (max_moments < 2 || (max_moments & 1)) KPM_THROW(KPM_EINVAL, "nmoments must be even and >= 2");
+    if (!(a > 0.0) || !std::isfinite(a) || !std::isfinite(b)) KPM_THROW(KPM_EINVAL, "need a > 0 and finite a, b");
+    const double x0 = (e0 - b) / a;
+    if (!std::isfinite(e0) || !(std::fabs(x0) <= 1.0))
+        KPM_THROW(KPM_EINVAL, "e0 must lie in [b - a, b + a]");
+    const int ncol = __builtin_popcount(mask);
+    c->rec_ncol = ncol;
+    c->rec_max_steps = max_moments / 2;
+    c->rec_a = a;
+    c->rec_b = b;
+    const size_t vb = (size_t)ncol * c->dim * c->esz();
+    c->vA.ensure(vb);
+    c->vB.ensure(vb);
+    c->vS.ensure(vb);
+    const size_t db = (size_t)ncol * c->rec_max_steps * 2 * sizeof(double);
+    c->dots.ensure(db);
+    c->moments_dev.ensure(db);
+    ensure_reduce_scratch(c, ncol);
+    const bool f64 = c->prec == KPM_FP64;
+    const int64_t dim = c->dim;
+    c->dfl_c.ensure(sizeof(double) * 8);
+    c->dfl_p.ensure((size_t)dim * 8);
+    c->dfl_a.ensure((size_t)dim * 8);
+    double* cc = c->dfl_c.as<double>();         // [0] |psi0|^2, [1] c0 of a column, [4 + col] c0^2
+    double* p = c->dfl_p.as<double>();
+    double* al = c->dfl_a.as<double>();
+    double* parts = c->partials.as<double>();
+    unsigned* cnt = c->counters.as<unsigned>();
+    KPM_CUDA(cudaMemcpyAsync(p, psi0, (size_t)dim * 8, cudaMemcpyDeviceToDevice, c->st));
+    dot_dev(p, p, dim, true, parts, cnt, cc, c->st);
+    scale_inplace(p, dim, true, cc, c->st);
+    int j = 0;
+    for (int comp = 0; comp < 3; ++comp) {
+        if (!((mask >> comp) & 1)) continue;
+        const double* d = c->d_dip.as<double>() + (int64_t)comp * c->n * c->n;
+        dipole_apply_f64(c->ta, *c->tb, d, psi0, al, c->st);
+        dot_dev(p, al, dim, true, parts, cnt, cc + 1, c->st);
+        deflate(al, p, dim, cc + 1, (char*)c->vB.p + (size_t)j * dim * c->esz(), f64, c->st);
+        square_into(cc + 1, cc + 4 + j, c->st);
+        ++j;
+    }
+    sigma_dispatch(c, c->vB.p, c->vS.p, ncol);
+    update_dispatch(c, c->vS.p, c->vB.p, c->vA.p, 1, c->dots.as<double>(), nullptr);
+    c->rec_prev = c->vB.p;
+    c->rec_cur = c->vA.p;
+    c->rec_steps = 1;
+    c->rec_deflated = true;
+    c->rec_x0 = x0;
     c->drop_graphs();
     c->step_ctr.ensure(sizeof(unsigned));
     step_set(c->step_ctr.as<unsigned>(), 1u, c->st);
@@ -447,7 +517,8 @@ void check_device_errors(kpm_ctx* c) {
 kpm_status rec_collect(kpm_ctx* c, double* out, int nm_stride) {
     int ns = c->rec_steps;
     doubling_combine(c->dots.as<double>(), c->rec_ncol, ns, (int64_t)c->rec_max_steps * 2,
-                     c->moments_dev.as<double>(), 2 * c->rec_max_steps, c->st);
+                     c->moments_dev.as<double>(), 2 * c->rec_max_steps,
+                     c->rec_deflated ? c->dfl_c.as<double>() + 4 : nullptr, c->rec_x0, c->st);
     for (int j = 0; j < c->rec_ncol; ++j)
         KPM_CUDA(cudaMemcpyAsync(out + (size_t)j * nm_stride,
                                  c->moments_dev.as<double>() + (size_t)j * 2 * c->rec_max_steps,
@@ -537,9 +608,13 @@ kpm_status kpm_create(const double* h1, const double* eri, const double* dipole,
                         }
                     wcol = std::fmax(wcol, col);
                 }
+            // the diagonal of H in FP64 (hi + lo floats), added exactly after the
+            // reduced-precision products, which leave it out
+            c->d_diag.alloc((size_t)c->dim * sizeof(float2));
+            exact_diagonal(c->ta, *c->tb, c->d_eri.as<double>(), norb, c->d_diag.as<float2>(), c->st);
             c->tc.reset(new TcSigma());
-            c->tc->init(c->ta, *c->tb, c->d_h1.as<double>(), c->d_eri.as<double>(), norb, wmax,
-                        wcol, prec == KPM_MIXED, c->st);
+            c->tc->init(c->ta, *c->tb, c->d_h1.as<double>(), c->d_eri.as<double>(),
+                        c->d_diag.as<float2>(), norb, wmax, wcol, prec == KPM_MIXED, c->st);
         }
         KPM_CUDA(cudaStreamSynchronize(c->st));
     });
@@ -651,6 +726,91 @@ kpm_status kpm_bounds(kpm_ctx* ctx, int iters, uint64_t seed, double* emin, doub
     });
 }
 
+kpm_status kpm_ground_state(kpm_ctx* ctx, int iters, int max_cycles, double tol, uint64_t seed,
+                            double* psi_dev, double* e0, double* resid) {
+    if (!ctx) { g_err = "NULL context"; return KPM_EINVAL; }
+    return guarded(ctx, [&] {
+        if (iters < 2 || iters > 4096 || max_cycles < 1 || max_cycles > 10000 || !psi_dev ||
+            !(tol > 0.0) || !e0 || !resid)
+            KPM_THROW(KPM_EINVAL, "bad ground-state arguments");
+        DeviceGuard g(ctx->device);
+        const int64_t dim = ctx->dim;
+        const int k = (int)std::min<int64_t>(iters, dim);
+        const bool f64 = ctx->prec == KPM_FP64;
+        const size_t vb = (size_t)dim * ctx->esz();
+        ctx->lz_v0.ensure(vb);
+        ctx->lz_v1.ensure(vb);
+        ctx->lz_w.ensure(vb);
+        ctx->lz_start.ensure(vb);
+        ctx->lz_ab.ensure(sizeof(double) * (6 * (k + 1)));
+        ctx->lz_scalar.ensure(sizeof(double) * 8);
+        ensure_reduce_scratch(ctx, 1);
+        double* al = ctx->lz_ab.as<double>();
+        double* be = al + (k + 1);
+        double* sv = be + (k + 1);          // eigenvector of T
+        double* scr = sv + (k + 1);         // 2k scratch
+        double* sc = ctx->lz_scalar.as<double>();
+        double* parts = ctx->partials.as<double>();
+        unsigned* cnt = ctx->counters.as<unsigned>();
+        void* start = ctx->lz_start.p;
+        fill_random(start, dim, f64, seed, ctx->st);
+        dot_dev(start, start, dim, f64, parts, cnt, sc, ctx->st);
+        scale_inplace(start, dim, f64, sc, ctx->st);
+        // one pass of k Lanczos steps from `start`; with `acc`, psi += s_j v_j as
+        // v_j is regenerated (the kernels are deterministic, so pass 2 repeats
+        // pass 1's vectors bit for bit)
+        auto pass = [&](bool acc) {
+            void* v = ctx->lz_v0.p;
+            void* vp = ctx->lz_v1.p;
+            void* w = ctx->lz_w.p;
+            KPM_CUDA(cudaMemcpyAsync(v, start, vb, cudaMemcpyDeviceToDevice, ctx->st));
+            for (int j = 0; j < k; ++j) {
+                if (acc) axpy_dev(psi_dev, v, dim, f64, sv + j, ctx->st);
+                if (acc && j == k - 1) break;
+                sigma_dispatch(ctx, v, w, 1);
+                dot_dev(w, v, dim, f64, parts, cnt, al + j, ctx->st);
+                lanczos_orth(w, v, j ? vp : nullptr, dim, f64, al + j, j ? be + j - 1 : nullptr,
+                             parts, cnt, sc, ctx->st);
+                lanczos_scale(vp, w, dim, f64, sc, be + j, ctx->st);
+                std::swap(v, vp);
+            }
+        };
+        double e = 0.0, r = INFINITY;
+        for (int cyc = 0; cyc < max_cycles; ++cyc) {
+            pass(false);
+            tridiag_lowest(al, be, k, sc + 4, sv, scr, ctx->st);
+            KPM_CUDA(cudaMemsetAsync(psi_dev, 0, (size_t)dim * 8, ctx->st));
+            pass(true);
+            // psi /= |psi|; residual |H psi - E psi| with E = <psi|H|psi>, in the
+            // context precision (psi rounded to it for the product)
+            dot_dev(psi_dev, psi_dev, dim, true, parts, cnt, sc, ctx->st);
+            scale_inplace(psi_dev, dim, true, sc, ctx->st);
+            void* v = ctx->lz_v0.p;
+            void* w = ctx->lz_w.p;
+            if (f64) KPM_CUDA(cudaMemcpyAsync(v, psi_dev, vb, cudaMemcpyDeviceToDevice, ctx->st));
+            else to_f32(psi_dev, (float*)v, dim, ctx->st);
+            sigma_dispatch(ctx, v, w, 1);
+            dot_dev(w, v, dim, f64, parts, cnt, sc + 1, ctx->st);
+            dot_dev(v, v, dim, f64, parts, cnt, sc + 2, ctx->st);
+            lanczos_orth(w, v, nullptr, dim, f64, sc + 1, nullptr, parts, cnt, sc + 3, ctx->st);
+            double h[4];
+            KPM_CUDA(cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, ctx->st));
+            KPM_CUDA(cudaStreamSynchronize(ctx->st));
+            check_device_errors(ctx);
+            // v is psi rounded to the context precision: |v| = 1 up to that rounding
+            e = h[1] / h[2];
+            r = std::sqrt(std::fmax(h[3], 0.0));
+            if (r <= tol) break;
+            // restart from psi
+            KPM_CUDA(cudaMemcpyAsync(start, v, vb, cudaMemcpyDeviceToDevice, ctx->st));
+            dot_dev(start, start, dim, f64, parts, cnt, sc, ctx->st);
+            scale_inplace(start, dim, f64, sc, ctx->st);
+        }
+        *e0 = e;
+        *resid = r;
+    });
+}
+
 kpm_status kpm_recursion_begin(kpm_ctx* ctx, const double* psi0_dev, unsigned comp_mask, double a,
                                double b, int max_moments) {
     if (!ctx) { g_err = "NULL context"; return KPM_EINVAL; }
@@ -658,6 +818,115 @@ kpm_status kpm_recursion_begin(kpm_ctx* ctx, const double* psi0_dev, unsigned co
         DeviceGuard g(ctx->device);
         rec_begin(ctx, psi0_dev, comp_mask, a, b, max_moments);
     });
+}
+
+kpm_status kpm_recursion_begin_deflated(kpm_ctx* ctx, const double* psi0_dev, double e0,
+                                        unsigned comp_mask, double a, double b, int max_moments) {
+    if (!ctx) { g_err = "NULL context"; return KPM_EINVAL; }
+    return guarded(ctx, [&] {
+        DeviceGuard g(ctx->device);
+        rec_begin_deflated(ctx, psi0_dev, e0, comp_mask, a, b, max_moments);
+    });
+}
+
+kpm_status kpm_moments_deflated(kpm_ctx* ctx, const double* psi0_dev, double e0,
+                                unsigned comp_mask, double a, double b, int nmoments,
+                                double* moments_host) {
+    if (!ctx) { g_err = "NULL context"; return KPM_EINVAL; }
+    kpm_status r = KPM_OK;
+    kpm_status s = guarded(ctx, [&] {
+        if (!moments_host) KPM_THROW(KPM_EINVAL, "NULL output");
+        DeviceGuard g(ctx->device);
+        rec_begin_deflated(ctx, psi0_dev, e0, comp_mask, a, b, nmoments);
+        rec_advance(ctx, nmoments / 2 - 1);
+        r = rec_collect(ctx, moments_host, nmoments);
+    });
+    return s != KPM_OK ? s : r;
+}
+
+kpm_status kpm_moments_cross(kpm_ctx* ctx, const double* psi0, const double* op_a,
+                             const double* op_b, double a, double b, int nmoments,
+                             double* moments_host) {
+    if (!ctx) { g_err = "NULL context"; return KPM_EINVAL; }
+    kpm_status r = KPM_OK;
+    kpm_status s = guarded(ctx, [&] {
+        if (!psi0 || !op_a || !op_b || !moments_host) KPM_THROW(KPM_EINVAL, "NULL argument");
+        if (nmoments < 2 || (nmoments & 1)) KPM_THROW(KPM_EINVAL, "nmoments must be even and >= 2");
+        if (!(a > 0.0) || !std::isfinite(a) || !std::isfinite(b))
+            KPM_THROW(KPM_EINVAL, "need a > 0 and finite a, b");
+        const int n = ctx->n;
+        check_sym(op_a, n, "op_a");
+        check_sym(op_b, n, "op_b");
+        DeviceGuard g(ctx->device);
+        kpm_ctx* c = ctx;
+        const int64_t dim = c->dim;
+        const bool f64 = c->prec == KPM_FP64;
+        // the dipole kernels apply -sum d_pq E_pq: upload -op
+        std::vector<double> neg((size_t)2 * n * n);
+        for (int i = 0; i < n * n; ++i) {
+            neg[i] = -op_a[i];
+            neg[(size_t)n * n + i] = -op_b[i];
+        }
+        c->x_ops.ensure(neg.size() * sizeof(double));
+        KPM_CUDA(cudaMemcpyAsync(c->x_ops.p, neg.data(), neg.size() * sizeof(double),
+                                 cudaMemcpyHostToDevice, c->st));
+        const int nsteps = nmoments / 2;
+        c->rec_ncol = 2;
+        c->rec_max_steps = nsteps;
+        c->rec_a = a;
+        c->rec_b = b;
+        c->rec_deflated = false;
+        const size_t vb = (size_t)2 * dim * c->esz();
+        c->vA.ensure(vb);
+        c->vB.ensure(vb);
+        c->vS.ensure(vb);
+        c->dots.ensure((size_t)2 * nsteps * 2 * sizeof(double));
+        c->moments_dev.ensure((size_t)nmoments * sizeof(double));
+        c->x_cross.ensure((size_t)nmoments * sizeof(double));
+        ensure_reduce_scratch(c, 2);
+        c->drop_graphs();
+        double* xc = c->x_cross.as<double>();
+        double* parts = c->partials.as<double>();
+        unsigned* cnt = c->counters.as<unsigned>() + 2;    // counters 0, 1: the update's columns
+        for (int j = 0; j < 2; ++j) {
+            const double* d = c->x_ops.as<double>() + (size_t)j * n * n;
+            void* y = (char*)c->vB.p + (size_t)j * dim * c->esz();
+            if (f64) dipole_apply_f64(c->ta, *c->tb, d, psi0, (double*)y, c->st);
+            else dipole_apply_f32(c->ta, *c->tb, d, psi0, (float*)y, c->st);
+        }
+        void* prev = c->vB.p;   // (a_0, b_0)
+        void* cur = c->vA.p;    // (a_1, b_1) after the first update
+        sigma_dispatch(c, prev, c->vS.p, 2);
+        update_dispatch(c, c->vS.p, prev, cur, 1, c->dots.as<double>(), nullptr);
+        cross_dots(prev, cur, dim, f64, parts, cnt, xc, c->st);
+        // prev = step k - 1, cur = step k
+        for (int k = 1; k < nsteps; ++k) {
+            sigma_dispatch(c, cur, c->vS.p, 2);
+            // update writes step n + 1 over step n - 1; its own dots (at index k) are unused
+            update_dispatch(c, c->vS.p, cur, prev, 0, c->dots.as<double>() + 2 * k, nullptr);
+            cross_dots(cur, prev, dim, f64, parts, cnt, xc + 2 * k, c->st);
+            std::swap(prev, cur);
+        }
+        cross_doubling(xc, nsteps, c->moments_dev.as<double>(), c->st);
+        double self[2];
+        KPM_CUDA(cudaMemcpyAsync(moments_host, c->moments_dev.p, sizeof(double) * nmoments,
+                                 cudaMemcpyDeviceToHost, c->st));
+        KPM_CUDA(cudaMemcpyAsync(&self[0], c->dots.as<double>(), sizeof(double),
+                                 cudaMemcpyDeviceToHost, c->st));
+        KPM_CUDA(cudaMemcpyAsync(&self[1], c->dots.as<double>() + (size_t)2 * nsteps,
+                                 sizeof(double), cudaMemcpyDeviceToHost, c->st));
+        KPM_CUDA(cudaStreamSynchronize(c->st));
+        check_device_errors(c);
+        c->rec_steps = 0;     // the context holds no resumable recursion now
+        const double lim = std::sqrt(std::fabs(self[0] * self[1])) * (1.0 + 1e-6);
+        for (int i = 0; i < nmoments; ++i)
+            if (!std::isfinite(moments_host[i]) || std::fabs(moments_host[i]) > lim) {
+                c->err = "|Omega_n| exceeds the Cauchy-Schwarz bound: [b-a, b+a] misses the spectrum";
+                r = KPM_EBOUNDS;
+                break;
+            }
+    });
+    return s != KPM_OK ? s : r;
 }
 
 kpm_status kpm_recursion_advance(kpm_ctx* ctx, int nsteps) {
@@ -757,7 +1026,7 @@ kpm_status kpm_spectrum(const double* moments, int nmoments, double a, double b,
                         int kernel, double* omega_out, double* intensity_out) {
     return guarded(nullptr, [&] {
         if (!moments || !omega_out || !intensity_out) KPM_THROW(KPM_EINVAL, "NULL argument");
-        if (nmoments < 1 || npoints < 1 || (kernel != 0 && kernel != 1))
+        if (nmoments < 1 || npoints < 1 || kernel < 0 || kernel > 2)
             KPM_THROW(KPM_EINVAL, "bad spectrum arguments");
         if (!(a > 0.0)) KPM_THROW(KPM_EINVAL, "a must be > 0");
         require_device();
@@ -769,6 +1038,28 @@ kpm_status kpm_spectrum(const double* moments, int nmoments, double a, double b,
         KPM_CUDA(cudaMemcpy(dm.p, moments, sizeof(double) * nmoments, cudaMemcpyHostToDevice));
         spectrum_dev(dm.as<double>(), nmoments, a, b, npoints, kernel, dd.as<double>(),
                      dom.as<double>(), din.as<double>(), nullptr);
+        KPM_CUDA(cudaMemcpy(omega_out, dom.p, sizeof(double) * npoints, cudaMemcpyDeviceToHost));
+        KPM_CUDA(cudaMemcpy(intensity_out, din.p, sizeof(double) * npoints, cudaMemcpyDeviceToHost));
+    });
+}
+
+kpm_status kpm_spectrum_lorentz(const double* moments, int nmoments, double a, double b,
+                                int npoints, double lambda, double* omega_out,
+                                double* intensity_out) {
+    return guarded(nullptr, [&] {
+        if (!moments || !omega_out || !intensity_out) KPM_THROW(KPM_EINVAL, "NULL argument");
+        if (nmoments < 1 || npoints < 1 || !(lambda > 0.0) || !std::isfinite(lambda))
+            KPM_THROW(KPM_EINVAL, "bad spectrum arguments");
+        if (!(a > 0.0)) KPM_THROW(KPM_EINVAL, "a must be > 0");
+        require_device();
+        DevBuf dm, dd, dom, din;
+        dm.alloc(sizeof(double) * nmoments);
+        dd.alloc(sizeof(double) * nmoments);
+        dom.alloc(sizeof(double) * npoints);
+        din.alloc(sizeof(double) * npoints);
+        KPM_CUDA(cudaMemcpy(dm.p, moments, sizeof(double) * nmoments, cudaMemcpyHostToDevice));
+        spectrum_dev(dm.as<double>(), nmoments, a, b, npoints, 2, dd.as<double>(),
+                     dom.as<double>(), din.as<double>(), nullptr, lambda);
         KPM_CUDA(cudaMemcpy(omega_out, dom.p, sizeof(double) * npoints, cudaMemcpyDeviceToHost));
         KPM_CUDA(cudaMemcpy(intensity_out, din.p, sizeof(double) * npoints, cudaMemcpyDeviceToHost));
     });
@@ -801,6 +1092,16 @@ kpm_status kpm_profile_read_rowpass(kpm_ctx* ctx, double* ms, int* count) {
         if (ms) *ms = t;
         if (count) *count = n;
     });
+}
+
+kpm_status kpm_test_rowpass_stall(kpm_ctx* ctx, int enable) {
+    if (!ctx) { g_err = "NULL context"; return KPM_EINVAL; }
+    if (!ctx->tc) {
+        ctx->err = "not a tensor-core (KPM_MIXED / KPM_MIXED_BF16) context";
+        return KPM_EINVAL;
+    }
+    ctx->tc->stall_next = enable != 0;
+    return KPM_OK;
 }
 
 kpm_status kpm_tuned_params(const kpm_ctx* ctx, int* group_beta, int* group_alpha) {

@@ -206,9 +206,21 @@ void cheb_update_f32(const float* s, const float* c, float* prev, int64_t dim, i
 void step_set(unsigned* step, unsigned v, cudaStream_t st);
 void step_inc(unsigned* step, cudaStream_t st);
 
-// moments[col][2n], [2n+1] from dots[col][n][2] (doubling identities).
+// moments[col][2n], [2n+1] from dots[col][n][2] (doubling identities); with defl
+// (deflated recursions) defl[col] T_n(x0) is added to moment n.
 void doubling_combine(const double* dots, int ncol, int nsteps, int64_t dots_col_stride,
-                      double* moments, int nmoments_stride, cudaStream_t st);
+                      double* moments, int nmoments_stride, const double* defl, double x0,
+                      cudaStream_t st);
+// al -= coef[0] p (FP64, in place) and out = al in the context precision.
+void deflate(double* al, const double* p, int64_t dim, const double* coef, void* out, bool f64,
+             cudaStream_t st);
+// Two-column block (a, b) cross dots: out[0] = <a_n|b_n> (cur), out[1] = <a_n+1|b_n>.
+void cross_dots(const void* cur, const void* next, int64_t dim, bool f64, double* partials,
+                unsigned* counters, double* out, cudaStream_t st);
+// Cross moments from the cross dots c[2n], c[2n+1] (doubling identities).
+void cross_doubling(const double* cross, int nsteps, double* moments, cudaStream_t st);
+// *c2 = (*c)^2 on the device.
+void square_into(const double* c, double* c2, cudaStream_t st);
 
 // Lanczos pieces (FP64 scalars on the device).
 void dot_dev(const void* x, const void* y, int64_t dim, bool f64, double* partials,
@@ -224,9 +236,19 @@ void scale_inplace(void* v, int64_t dim, bool f64, const double* norm2, cudaStre
 void tridiag_extremes(const double* alpha, const double* beta, int k, double* out4,
                       double* scratch, cudaStream_t st);
 
+// Lowest eigenpair of a k x k symmetric tridiagonal (device): *theta and the unit
+// eigenvector s[0..k); scratch: 2k doubles.
+void tridiag_lowest(const double* alpha, const double* beta, int k, double* theta, double* s,
+                    double* scratch, cudaStream_t st);
+// acc += coef[0] * v, acc FP64 [dim], v FP64 or FP32; coef read on the device.
+void axpy_dev(double* acc, const void* v, int64_t dim, bool f64, const double* coef,
+              cudaStream_t st);
+
 // Spectrum on the device: moments (device) -> omega, intensity (device);
 // `damped` is device scratch of N doubles (g_n Omega_n with the factor 2 for n >= 1).
+// kernel: 0 none, 1 Jackson, 2 Lorentz with parameter lambda.
 void spectrum_dev(const double* moments, int N, double a, double b, int M, int kernel,
-                  double* damped, double* omega, double* intensity, cudaStream_t st);
+                  double* damped, double* omega, double* intensity, cudaStream_t st,
+                  double lambda = KPM_LORENTZ_LAMBDA);
 
 }  // namespace kpm

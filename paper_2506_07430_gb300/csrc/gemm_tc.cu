@@ -14,9 +14,10 @@
 //
 // Operands are split into two FP16 pieces with power-of-two scales (x = hi + lo);
 // three MMAs per k-step (A_hi B_hi + A_lo B_hi + A_hi B_lo) accumulate in FP32
-// in tensor memory.  The diagonals of F_a, F_b are kept out of the split matrices
-// and added exactly in the epilogue of the alpha product (FP64 values stored as
-// float hi + lo), together with nothing else.
+// in tensor memory.  The diagonals of F_a, F_b are kept out of the split matrices;
+// the epilogue of the alpha product adds the whole diagonal of H (same-spin
+// diagonals and the opposite-spin Coulomb sums, evaluated in FP64 and stored as
+// float hi + lo per determinant) times x, hi and lo multiplied separately.
 //
 // Kernel: CTA tile 128 x 256, k-block 64 (128 bytes per row: one SWIZZLE_128B
 // atom row), two-stage TMA pipeline (full/empty mbarriers), one warp issues TMA,
@@ -146,10 +147,10 @@ struct GemmArgs {
     float scale;               // or, if amax != nullptr, scale / (sa(amax)) with the operand scale
     const float* amax;         // max |x| of the split vector operand (operand scale), or null
     float wscale;              // scale of the matrix operand
-    // exact diagonal term: y[n*ldy+m] += (dn[n] + dm[m]) * x[n*ldy+m]  (if x != nullptr)
+    // exact diagonal term (if x != nullptr): y[n*ldy+m] += d[n*ldy+m] * x[n*ldy+m], the
+    // diagonal H_II evaluated in FP64 and stored as float (hi, lo)
     const float* x;
-    const float2* dm;
-    const float2* dn;
+    const float2* dfull;
     int* err;
     int group_m;               // row tiles per rasterisation group (tuned; see DenseSS::autotune)
 };
@@ -333,8 +334,6 @@ k_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensor
             }
             const int m = m0 + quad * 32 + lane;
             if (m < g.M) {
-                float2 dmv = make_float2(0.f, 0.f);
-                if (g.x) dmv = g.dm[m];
 #pragma unroll
                 for (int u = 0; u < 128; ++u) {
                     const int n = n0 + h * 128 + u;
@@ -342,9 +341,10 @@ k_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensor
                         const int64_t o = (int64_t)n * g.ldy + m;
                         float v = g.y[o] + rs[u] * scale;
                         if (g.x) {
-                            const float2 dn = g.dn[n];
+                            // hi and lo multiply separately: the diagonal keeps its FP64 value
+                            const float2 d = g.dfull[o];
                             const float xv = g.x[o];
-                            v = fmaf(dmv.x + dn.x, xv, fmaf(dmv.y + dn.y, xv, v));
+                            v = fmaf(d.x, xv, fmaf(d.y, xv, v));
                         }
                         g.y[o] = v;
                     }
@@ -584,7 +584,7 @@ void DenseSS::launch_beta(float* y, const float* amax, int group, cudaStream_t s
     CUtensorMap b0 = make_map(xh.as<__half>(), na, nb, xpitch, GM_BN);
     CUtensorMap b1 = make_map(xl.as<__half>(), na, nb, xpitch, GM_BN);
     GemmArgs g{(int)nb, (int)na, (int)nb, y, nb, 1.0f, amax, (float)wscale_b,
-               nullptr, nullptr, nullptr, err, group};
+               nullptr, nullptr, err, group};
     dim3 grid((unsigned)(((nb + GM_BM - 1) / GM_BM) * ((na + GM_BN - 1) / GM_BN)));
     k_gemm<<<grid, GM_THREADS, smem, st>>>(a0, a1, b0, b1, g);
     KPM_LAUNCHED();
@@ -593,12 +593,13 @@ void DenseSS::launch_beta(float* y, const float* amax, int group, cudaStream_t s
 // alpha: out[m = I_b][n = I_a] = sum_J x^T[I_b][J] Fa[I_a][J], plus the exact diagonals
 void DenseSS::launch_alpha(const float* x, float* y, const float* amax, int group,
                            cudaStream_t st) {
+    const float* diag = diag_full ? x : nullptr;
     CUtensorMap a0 = make_map(th.as<__half>(), nb, na, pa, GM_BM);
     CUtensorMap a1 = make_map(tl.as<__half>(), nb, na, pa, GM_BM);
     CUtensorMap b0 = make_map(fa_hi->as<__half>(), na, na, pa, GM_BN);
     CUtensorMap b1 = make_map(fa_lo->as<__half>(), na, na, pa, GM_BN);
     GemmArgs g{(int)nb, (int)na, (int)na, y, nb, 1.0f, amax, (float)wscale_a,
-               x, db.as<float2>(), da->as<float2>(), err, group};
+               diag, diag ? diag_full : nullptr, err, group};
     dim3 grid((unsigned)(((nb + GM_BM - 1) / GM_BM) * ((na + GM_BN - 1) / GM_BN)));
     k_gemm<<<grid, GM_THREADS, smem, st>>>(a0, a1, b0, b1, g);
     KPM_LAUNCHED();

@@ -21,13 +21,18 @@ struct DenseSS {
     DevBuf fmax;                              // scratch for max |F_off|
     size_t smem = 0;
     int* err = nullptr;
+    // exact diagonal H_II of the whole H (same-spin diagonals and the opposite-spin
+    // Coulomb sum, FP64 stored as float hi + lo, [N_a][N_b]), added by the alpha
+    // product's epilogue; the split matrices and the row pass leave it out
+    const float2* diag_full = nullptr;
 
     // Builds the split matrices; `same`: alpha and beta strings are identical.
     void init(const SpinTables& A, const SpinTables& B, bool same, int* err_flag,
               cudaStream_t st);
     // xh/xl = x split into scaled FP16 pieces [N_a][xpitch] (zero padding).
     void split(const float* x, const float* amax, cudaStream_t st);
-    // y += (F_a (x) 1 + 1 (x) F_b) x, the diagonals exactly; amax = device max|x|.
+    // y += (F_a (x) 1 + 1 (x) F_b) x with the off-diagonal parts of F_a, F_b, plus
+    // diag_full * x (the whole exact diagonal of H); amax = device max|x|.
     // Uses xh/xl from split(x) on the same stream.
     void apply(const float* x, float* y, const float* amax, cudaStream_t st);
     // Rasterisation group (row tiles per group) of the beta and alpha GEMMs, chosen

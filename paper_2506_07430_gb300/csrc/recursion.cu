@@ -106,7 +106,12 @@ __device__ __forceinline__ void cheb_update_cta(int blk, int nblk, int col,
             tt += nx * cv;
         }
     } else {
-        const float k1 = (float)((first ? 1.0 : 2.0) / a), k2 = (float)(b * (first ? 1.0 : 2.0) / a);
+        // k1 = 2/a and k2 = 2b/a as float pairs (hi + lo): rounding them to one float
+        // each would shift every eigenvalue of H~ by the same relative 2^-24, an
+        // error that grows linearly with the moment index
+        const double k1d = (first ? 1.0 : 2.0) / a, k2d = b * k1d;
+        const float k1 = (float)k1d, k1l = (float)(k1d - (double)k1);
+        const float k2 = (float)k2d, k2l = (float)(k2d - (double)k2);
         int64_t i = (int64_t)blk * blockDim.x + threadIdx.x;
         while (i < dim) {
             float gs = 0.f, gt = 0.f;
@@ -114,7 +119,8 @@ __device__ __forceinline__ void cheb_update_cta(int blk, int nblk, int col,
             for (int u = 0; u < 4; ++u) {
                 if (i < dim) {
                     float cv = c[i];
-                    float nx = fmaf(k1, s[i], -k2 * cv);
+                    const float sv = s[i];
+                    float nx = fmaf(k1, sv, fmaf(-k2, cv, fmaf(k1l, sv, -k2l * cv)));
                     if (!first) nx -= prev[i];
                     prev[i] = nx;
                     gs = fmaf(cv, cv, gs);
@@ -217,8 +223,10 @@ void step_inc(unsigned* step, cudaStream_t st) {
     KPM_LAUNCHED();
 }
 
+// With `defl` (deflated recursion, see rec_begin_deflated): the permanent-dipole
+// term defl[col] T_n(x0), T_n(x0) = cos(n arccos x0), is added to moment n.
 __global__ void k_doubling(const double* __restrict__ dots, int nsteps, int64_t dstride,
-                           double* __restrict__ mom, int mstride) {
+                           double* __restrict__ mom, int mstride, const double* defl, double x0) {
     const int col = blockIdx.y;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= nsteps) return;
@@ -226,15 +234,94 @@ __global__ void k_doubling(const double* __restrict__ dots, int nsteps, int64_t 
     double s0 = d[0], t0 = d[1];
     double sn = d[2 * n], tn = d[2 * n + 1];
     double* m = mom + (int64_t)col * mstride;
-    m[2 * n] = n == 0 ? s0 : 2.0 * sn - s0;
-    m[2 * n + 1] = n == 0 ? t0 : 2.0 * tn - t0;
+    double m0 = n == 0 ? s0 : 2.0 * sn - s0;
+    double m1 = n == 0 ? t0 : 2.0 * tn - t0;
+    if (defl) {
+        const double th = acos(x0), c2 = defl[col];
+        m0 += c2 * cos((double)(2 * n) * th);
+        m1 += c2 * cos((double)(2 * n + 1) * th);
+    }
+    m[2 * n] = m0;
+    m[2 * n + 1] = m1;
 }
 
 void doubling_combine(const double* dots, int ncol, int nsteps, int64_t dstride, double* moments,
-                      int mstride, cudaStream_t st) {
+                      int mstride, const double* defl, double x0, cudaStream_t st) {
     if (nsteps <= 0) return;
     dim3 grid((nsteps + 127) / 128, ncol);
-    k_doubling<<<grid, 128, 0, st>>>(dots, nsteps, dstride, moments, mstride);
+    k_doubling<<<grid, 128, 0, st>>>(dots, nsteps, dstride, moments, mstride, defl, x0);
+    KPM_LAUNCHED();
+}
+
+// Cross dots of a two-column block recursion (columns a, b): out[0] = <a_n|b_n>
+// from cur, out[1] = <a_n+1|b_n> from next (column a) and cur (column b).
+template <class T>
+__global__ void __launch_bounds__(RED_THREADS)
+k_cross_dots(const T* __restrict__ cur, const T* __restrict__ next, int64_t dim, double* partials,
+             unsigned* counter, double* out) {
+    double u = 0.0, v = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim; i += stride) {
+        const double bn = (double)cur[dim + i];
+        u += (double)cur[i] * bn;
+        v += (double)next[i] * bn;
+    }
+    finish_reduce(u, v, partials, counter, gridDim.x, blockIdx.x, out, out + 1);
+}
+
+void cross_dots(const void* cur, const void* next, int64_t dim, bool f64, double* partials,
+                unsigned* counters, double* out, cudaStream_t st) {
+    int g = reduce_blocks(dim);
+    if (f64)
+        k_cross_dots<double><<<g, RED_THREADS, 0, st>>>((const double*)cur, (const double*)next,
+                                                        dim, partials, counters, out);
+    else
+        k_cross_dots<float><<<g, RED_THREADS, 0, st>>>((const float*)cur, (const float*)next, dim,
+                                                       partials, counters, out);
+    KPM_LAUNCHED();
+}
+
+// Omega_0 = c[0], Omega_1 = c[1], Omega_2n = 2 c[2n] - c[0], Omega_2n+1 = 2 c[2n+1] - c[1]
+__global__ void k_cross_doubling(const double* __restrict__ c, int nsteps, double* __restrict__ m) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nsteps) return;
+    m[2 * n] = n == 0 ? c[0] : 2.0 * c[2 * n] - c[0];
+    m[2 * n + 1] = n == 0 ? c[1] : 2.0 * c[2 * n + 1] - c[1];
+}
+
+void cross_doubling(const double* cross, int nsteps, double* moments, cudaStream_t st) {
+    if (nsteps <= 0) return;
+    k_cross_doubling<<<(nsteps + 127) / 128, 128, 0, st>>>(cross, nsteps, moments);
+    KPM_LAUNCHED();
+}
+
+// a[i] -= coef[0] * p[i]; out (context precision) = a, FP64 in place
+template <class T>
+__global__ void k_deflate(double* __restrict__ al, const double* __restrict__ p, int64_t dim,
+                          const double* coef, T* __restrict__ out) {
+    const double c = *coef;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim; i += stride) {
+        const double v = al[i] - c * p[i];
+        al[i] = v;
+        out[i] = (T)v;
+    }
+}
+
+void deflate(double* al, const double* p, int64_t dim, const double* coef, void* out, bool f64,
+             cudaStream_t st) {
+    int g = reduce_blocks(dim);
+    if (f64) k_deflate<double><<<g, RED_THREADS, 0, st>>>(al, p, dim, coef, (double*)out);
+    else k_deflate<float><<<g, RED_THREADS, 0, st>>>(al, p, dim, coef, (float*)out);
+    KPM_LAUNCHED();
+}
+
+__global__ void k_square_into(const double* __restrict__ c, double* __restrict__ c2) {
+    *c2 = (*c) * (*c);
+}
+
+void square_into(const double* c, double* c2, cudaStream_t st) {
+    k_square_into<<<1, 1, 0, st>>>(c, c2);
     KPM_LAUNCHED();
 }
 
@@ -432,6 +519,78 @@ __global__ void k_tridiag(const double* al, const double* be, int k, double* out
 void tridiag_extremes(const double* alpha, const double* beta, int k, double* out4,
                       double* scratch, cudaStream_t st) {
     k_tridiag<<<1, 1, 0, st>>>(alpha, beta, k, out4, scratch);
+    KPM_LAUNCHED();
+}
+
+// Lowest eigenpair of the k x k symmetric tridiagonal T: theta by Sturm
+// bisection, its unit eigenvector s by inverse iteration with the tridiagonal
+// (Thomas) solver, shifted just below theta.  out[0] = theta, s_out[0..k).
+__global__ void k_tridiag_lowest(const double* al, const double* be, int k, double* out,
+                                 double* s_out, double* w) {
+    if (threadIdx.x || blockIdx.x) return;
+    double lo = al[0], hi = al[0];
+    for (int i = 0; i < k; ++i) {
+        double r = (i ? fabs(be[i - 1]) : 0.0) + (i + 1 < k ? fabs(be[i]) : 0.0);
+        lo = fmin(lo, al[i] - r);
+        hi = fmax(hi, al[i] + r);
+    }
+    lo -= 1e-9 * (1.0 + fabs(lo));
+    hi += 1e-9 * (1.0 + fabs(hi));
+    const double th = tri_eig(al, be, k, 0, lo, hi);
+    double* c = w;
+    double* d = w + k;
+    double scale = 0.0;
+    for (int i = 0; i < k; ++i) scale = fmax(scale, fabs(al[i]) + (i + 1 < k ? fabs(be[i]) : 0.0));
+    const double shift = th - 1e-12 * (scale + 1e-300);
+    for (int i = 0; i < k; ++i) s_out[i] = 1.0;
+    for (int it = 0; it < 6; ++it) {
+        double piv = al[0] - shift;
+        if (fabs(piv) < 1e-300) piv = 1e-300;
+        c[0] = (k > 1 ? be[0] : 0.0) / piv;
+        d[0] = s_out[0] / piv;
+        for (int i = 1; i < k; ++i) {
+            piv = (al[i] - shift) - be[i - 1] * c[i - 1];
+            if (fabs(piv) < 1e-300) piv = 1e-300;
+            c[i] = (i + 1 < k ? be[i] : 0.0) / piv;
+            d[i] = (s_out[i] - be[i - 1] * d[i - 1]) / piv;
+        }
+        s_out[k - 1] = d[k - 1];
+        for (int i = k - 2; i >= 0; --i) s_out[i] = d[i] - c[i] * s_out[i + 1];
+        double nrm = 0.0;
+        for (int i = 0; i < k; ++i) nrm += s_out[i] * s_out[i];
+        nrm = sqrt(nrm);
+        if (!(nrm > 0.0) || !isfinite(nrm)) {
+            for (int i = 0; i < k; ++i) s_out[i] = i == 0 ? 1.0 : 0.0;
+            break;
+        }
+        for (int i = 0; i < k; ++i) s_out[i] /= nrm;
+    }
+    out[0] = th;
+}
+
+void tridiag_lowest(const double* alpha, const double* beta, int k, double* theta, double* s,
+                    double* scratch, cudaStream_t st) {
+    k_tridiag_lowest<<<1, 1, 0, st>>>(alpha, beta, k, theta, s, scratch);
+    KPM_LAUNCHED();
+}
+
+// acc[i] += coef[0] * v[i] (FP64 accumulation; the coefficient is read on the device)
+template <class T>
+__global__ void k_axpy_dev(double* __restrict__ acc, const T* __restrict__ v, int64_t dim,
+                           const double* coef) {
+    const double c = *coef;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim; i += stride)
+        acc[i] += c * (double)v[i];
+}
+
+void axpy_dev(double* acc, const void* v, int64_t dim, bool f64, const double* coef,
+              cudaStream_t st) {
+    int g = reduce_blocks(dim);
+    if (f64)
+        k_axpy_dev<double><<<g, RED_THREADS, 0, st>>>(acc, (const double*)v, dim, coef);
+    else
+        k_axpy_dev<float><<<g, RED_THREADS, 0, st>>>(acc, (const float*)v, dim, coef);
     KPM_LAUNCHED();
 }
 

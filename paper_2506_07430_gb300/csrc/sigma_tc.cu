@@ -15,11 +15,12 @@
 //   sigma[R, tgt_f] += sgn_f G[J][slot(f)]   for every f in tab(J)        (scatter)
 // (<I|E_pq|J> = <J|E_qp|I> turns the outer excitation into a scatter from J.)
 //
-// GEMM per tile: M = 128 columns J, K = KR (the row's nexc entries rounded up
-// to 16), N = P (NS + 1 rounded up to 16), operands in shared memory, D in
-// tensor memory (FP32).  Operands are split into two 16-bit pieces each (FP16
-// with power-of-two scales, or BF16), and three MMAs keep every product term
-// above 2^-22 relative: A_hi B_0, A_hi B_1, A_lo B_0.  The epilogue reads D
+// GEMM per tile: M = 128 columns J, K = KR (the row's off-diagonal entries plus
+// one column for its diagonal entries, rounded up to 16), N = P (NS + 1 rounded
+// up to 16), operands in shared memory, D in tensor memory (FP32).  x and W are
+// split into NW = 2 16-bit pieces each (FP16 with power-of-two scales, or BF16);
+// the MMAs A_hi B_j (every piece j of W) and A_lo B_0 drop only A_lo B_1, below
+// 2^-22 relative.  The epilogue reads D
 // (tcgen05.ld) and scatters into the row's sigma in shared memory with 32-bit
 // fixed-point integer atomics (order-independent, so the result is
 // reproducible bit for bit).  One CTA per SM, persistent over rows; the kernel
@@ -38,6 +39,7 @@ namespace kpm {
 namespace {
 
 constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+constexpr long long STALL_WAIT_CYCLES = 20000000LL;  // ~10 ms: the stall test's limit
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -149,25 +151,25 @@ struct RowPass {
     const uint4* tslot8;     // [P/8][Nc]: 8 16-bit entries per chunk of 8 slots (slot 8c+u in
                              // half u of the 128-bit word): target string | sign << 15,
                              // Nc + (J mod 32) when the slot of column J is absent
-    const int32_t* rtgt;     // [Nr][rnexc] row-string targets
-    const uint16_t* rslot;   // [Nr][rnexc] row-string slot | sign << 15
-    int rnexc;               // table entries per row string
-    int KR;                  // K of the row GEMM: rnexc rounded up to 16
+    const int32_t* rtgt;     // [Nr][rnexc] row-string targets of the off-diagonal entries
+    const uint16_t* rslot;   // [Nr][rnexc] their slot | sign << 15
+    int rnexc;               // off-diagonal table entries per row string, m (n - m)
+    int ndiag;               // 1 if the row strings hold electrons (a diagonal column), else 0
+    int KR;                  // K of the row GEMM: rnexc + ndiag rounded up to 16 (at least 16)
+    const uint32_t* rmask;   // [Nr] occupation masks of the row strings
+    const double* wdiag;     // [n][P] W[qq][s] (unscaled, FP64; zero for diagonal slots s)
     const uint16_t* wrow;    // W by input slot: NW pieces of [P][P] 16-bit (bits of the format)
     uint32_t ncols;          // TMEM columns allocated
     const float* amax;       // device max|x| (operand scaling)
     const float* rowmax;     // [Nr] max |x| of each row (per-row fixed-point range)
     float wscale;            // power-of-two scale applied to W in the image
-    float gbound;            // max over output slots of sum_k |W[k][s]| (unscaled W)
     int nexc_c;              // table entries per column string (contributions per target)
     int NS;                  // slots in use (n(n+1)/2); slots [NS, P) are padding
     int nst;                 // A stages in shared memory (2 or 3)
-    int shift;               // fixed-point scale = 2^shift x the a-priori one (see k_rowpass)
-    const int* rows;         // if set: process rows rows[0 .. *nrows) only
-    const int* nrows;
-    int* flagged;            // if set: rows whose range check failed are appended here
-    int* nflagged;
     int* err;
+    long long wait_cycles;   // limit of every mbarrier wait (clock64 cycles)
+    int stall;               // test of the bounded waits: the MMA thread issues nothing, so
+                             // the other roles' waits run out and the kernel reports it
 };
 
 constexpr int RP_SCATTER_WARPS = 16;         // 4 per TMEM lane quadrant
@@ -181,11 +183,6 @@ static_assert(RP_COPY_WARPS * 32 >= RP_MAXK, "one copy lane per entry (L2 prefet
 // Nc + (J mod 32), so the scatter adds every slot without a branch and the 32
 // lanes of a warp (32 consecutive J) sink into 32 different banks
 constexpr int RP_SINK = 32;
-// first-pass fixed-point scale: 2^RP_SHIFT times the per-row a-priori one (the
-// largest term of a dense vector's row is typically ~1/7 of that row's per-term
-// bound, so a factor 4 leaves margin and rows are rarely redone; rows whose terms
-// come within the 32-bit headroom are redone at the a-priori scale)
-constexpr int RP_SHIFT = 2;
 // poll interval of the copy and MMA warps' waits (the MMA of tile t + 1 has
 // about one scatter duration of slack, microseconds)
 #ifndef RP_BACKOFF_NS
@@ -199,27 +196,31 @@ constexpr int RP_SHIFT = 2;
 constexpr uint32_t A_LBO = 2048;             // A stage: K-group (8 entries) stride, bytes
 constexpr uint32_t A_SBO = 128;              // A stage: MN-group (8 columns) stride, bytes
 
-// operand scales, all powers of two (see the kernel comment)
-struct Scales {
-    float sa;      // x -> A
-    float fx;      // value -> fixed point
-    float bscale;  // W image -> B_R, so that D = value * fx
-};
-__device__ __forceinline__ Scales scales(float mx, bool fp16, float wscale, float gbound,
-                                         int nexc_c, int shift) {
-    Scales c{1.f, 1.f, 1.f};
-    if (mx > 0.f && isfinite(mx)) {
-        int e;
-        frexpf(mx, &e);  // mx < 2^e
-        if (fp16) c.sa = ldexpf(1.f, 14 - max(e, -90));
-        // every target receives nexc_c terms of magnitude <= max|x| gbound
-        const float bound = 1.02f * (float)nexc_c * mx * gbound;
-        int f = -90;
-        if (bound > 0.f) frexpf(bound, &f);  // bound < 2^f
-        c.fx = ldexpf(1.f, 31 + shift - max(f, -90));
+// operand scale of x (power of two): FP16 pieces of x * sa stay below 2^15
+__device__ __forceinline__ float x_scale(float mx, bool fp16) {
+    if (!fp16 || !(mx > 0.f) || !isfinite(mx)) return 1.f;
+    int e;
+    frexpf(mx, &e);  // mx < 2^e
+    return ldexpf(1.f, 14 - max(e, -90));
+}
+
+// value -> NW 16-bit pieces, each the rounding of what the previous ones left
+template <bool FP16, int NW>
+__device__ __forceinline__ void split16(double v, uint16_t (&out)[NW]) {
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+        double part;
+        if (FP16) {
+            const __half h = __double2half(v);
+            out[j] = __half_as_ushort(h);
+            part = (double)__half2float(h);
+        } else {
+            const __nv_bfloat16 h = __double2bfloat16(v);
+            out[j] = __bfloat16_as_ushort(h);
+            part = (double)__bfloat162float(h);
+        }
+        v -= part;
     }
-    c.bscale = c.fx / (c.sa * wscale);
-    return c;
 }
 
 template <bool FP16>
@@ -269,12 +270,12 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* mbar, uint32_t par
 // take a large share of its sub-partition's issue slots from the scatter warps;
 // roles off the critical path sleep backoff_ns between polls.
 __device__ __forceinline__ bool wait_phase(uint64_t* mbar, uint32_t parity, volatile int* abort_flag,
-                                           int* err, unsigned backoff_ns = 0) {
+                                           int* err, long long limit, unsigned backoff_ns = 0) {
     const long long t0 = clock64();
     while (!mbar_try_wait_sleep(mbar, parity)) {
         if (backoff_ns) __nanosleep(backoff_ns);
         if (*abort_flag) return false;
-        if (clock64() - t0 > WAIT_CYCLES) {
+        if (clock64() - t0 > limit) {
             *abort_flag = 1;
             atomicExch(err, 1);
             return false;
@@ -319,14 +320,16 @@ __device__ __forceinline__ bool wait_phase(uint64_t* mbar, uint32_t parity, vola
 //
 // Fixed-point range: integer addition wraps, so only each final row sum has to
 // fit in 32 bits, and it does whenever every term |D| < 2^31 / nexc_c.  Per row
-// R, |D[J][s]| <= c_s = sum_e rowmax(tgt_e) |W[slot e][s]| (rowmax: max |x| of a
-// source row), which sets the row's a-priori scale (capped so that B_R stays in
-// range); vectors with small or empty source rows get a correspondingly finer
-// step.  The first launch runs at a scale 2^shift finer than that bound; the
-// scatter warps track max |D| per row, and a row that reaches the limit is not
-// written but appended to a list that the second launch (shift = 0, rows from
-// the list) recomputes.  Which rows take the
-// second pass depends only on the data, so results stay reproducible.
+// R, |D[J][s]| <= c_s = sum_e rowmax(tgt_e) |B[s][e]| / fx (rowmax: max |x| of a
+// source row), which sets the row's scale fx (a power of two; capped so that B_R
+// stays in the FP16 range); vectors with small or empty source rows get a
+// correspondingly finer step.
+//
+// The row's m diagonal entries E_qq (q in R) all read source row R itself with
+// sign +1, so they share one K column: A = x[R][J], B = w_R[s] = sum_{q in R}
+// W[qq][s], formed in FP64 and split into NW pieces.  The block of W where both
+// excitations are diagonal ((pp|qq)) is zero in the image and in w_R: that part
+// of the diagonal of H is added exactly by the same-spin GEMM's epilogue.
 template <int P, bool FP16, int NW>
 __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
     constexpr int MAXF = P >= 32 ? P / 32 : 1;     // full chunks per scatter warp (upper bound)
@@ -346,14 +349,15 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
         (reinterpret_cast<uintptr_t>(rsl + RP_MAXK) + 15) & ~uintptr_t(15));  // [RP_MAXK]
     float* rsc = rmx + RP_MAXK;                                       // [4] row scales
     unsigned* rred = reinterpret_cast<unsigned*>(rsc + 4);            // [2] row reductions
-    uintptr_t tail = (reinterpret_cast<uintptr_t>(rred + 2) + 15) & ~uintptr_t(15);
+    double* wdg = reinterpret_cast<double*>(
+        (reinterpret_cast<uintptr_t>(rred + 2) + 15) & ~uintptr_t(15));  // [P] w_R (FP64)
+    uintptr_t tail = (reinterpret_cast<uintptr_t>(wdg + P) + 15) & ~uintptr_t(15);
     uint64_t* afree = reinterpret_cast<uint64_t*>(tail);   // [3] stage s free (MMA done)
     uint64_t* afull = afree + 3;                           // [3] stage s copied
     uint64_t* dfull = afree + 6;                           // [2] D buffer d written
     uint64_t* dfree = afree + 8;                           // [2] D buffer d read (16 warps)
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(afree + 10);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
-    volatile int* range_flag = abort_flag + 1;             // this row failed the range check
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -382,11 +386,9 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
     const uint32_t sA_addr = smem_u32(sA), sB_addr = smem_u32(sB);
     const uint32_t SBO_B = 16u * (uint32_t)KR;
     const int ntiles = (int)((Nc + 127) / 128);
-    const Scales sc = scales(*p.amax, FP16, p.wscale, p.gbound, p.nexc_c, p.shift);
-    // every target receives at most nexc_c terms: if each |D| (fixed-point units)
-    // stays below this limit, every row sum fits in 32 bits
-    const float dlimit = floorf(2147483648.f / (float)p.nexc_c) - 1.f;
-    const int64_t nrows = p.rows ? (int64_t)*p.nrows : p.Nr;
+    const float sa = x_scale(*p.amax, FP16);
+    const int64_t nrows = p.Nr;
+    const int ncolk = p.rnexc + p.ndiag;                   // K columns in use
 
     // scatter geometry (warps 0-15): used chunks of 8 slots, full chunks per
     // warp, and the remainder shared out two slots at a time
@@ -403,25 +405,40 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
     uint32_t g = 0;
 
     for (int64_t idx = blockIdx.x; idx < nrows; idx += gridDim.x) {
-        const int64_t ir = p.rows ? (int64_t)p.rows[idx] : idx;
+        const int64_t ir = idx;
         // ---- row set-up: zero sigma; the row's source rows, slots and signs; B_R
         if (tid == 0) {
-            *range_flag = 0;
             rred[0] = 0u;
             rred[1] = 0u;
         }
         for (int64_t j = tid; j < Nc + RP_SINK; j += RP_THREADS) srow[j] = 0;
         for (int e = tid; e < RP_MAXK; e += RP_THREADS) {
-            const bool in = e < p.rnexc;
-            rowoff[e] = in ? (int64_t)p.rtgt[ir * p.rnexc + e] * p.xpitch : -1;
-            rsl[e] = in ? p.rslot[ir * p.rnexc + e] : (uint16_t)0xFFFFu;
-            rmx[e] = in ? p.rowmax[p.rtgt[ir * p.rnexc + e]] : 0.f;
+            // off-diagonal entries, then the diagonal column (marker 0xFFFE), then padding
+            if (e < p.rnexc) {
+                const int32_t t = p.rtgt[ir * p.rnexc + e];
+                rowoff[e] = (int64_t)t * p.xpitch;
+                rsl[e] = p.rslot[ir * p.rnexc + e];
+                rmx[e] = p.rowmax[t];
+            } else if (e < ncolk) {
+                rowoff[e] = ir * p.xpitch;
+                rsl[e] = (uint16_t)0xFFFEu;
+                rmx[e] = p.rowmax[ir];
+            } else {
+                rowoff[e] = -1;
+                rsl[e] = (uint16_t)0xFFFFu;
+                rmx[e] = 0.f;
+            }
         }
         __syncthreads();
-        // this row's fixed-point range: |D[J][s]| <= c_s = sum_e rowmax(tgt_e) |W[slot e][s]|
-        // (piece 0 of W is within 2^-8 of W in either format: 1 % margin)
+        // w_R[s] in FP64; this row's fixed-point range c_s (in units of the W image;
+        // piece 0 of W is within 2^-8 of W in either format: 1 % margin) and max |B|
         if (tid < P) {
-            float c = 0.f, wm = 0.f;
+            double wr = 0.0;
+            for (uint32_t mk = __ldg(p.rmask + ir); mk; mk &= mk - 1)
+                wr += __ldg(p.wdiag + (size_t)(__ffs(mk) - 1) * P + tid);
+            wdg[tid] = wr;
+            const float wrs = (float)fabs(wr) * p.wscale;
+            float c = p.ndiag ? rmx[p.rnexc] * wrs : 0.f, wm = p.ndiag ? wrs : 0.f;
             for (int e = 0; e < p.rnexc; ++e) {
                 const float w = fabsf(f16bits<FP16>(__ldg(p.wrow + (size_t)(rsl[e] & 0x7FFFu) * P + tid)));
                 c = fmaf(rmx[e], w, c);
@@ -440,35 +457,42 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
             if (bound > 0.f && isfinite(bound)) {
                 int f;
                 frexpf(bound, &f);  // bound < 2^f
-                fx = ldexpf(1.f, 31 + p.shift - max(f, -90));
+                fx = ldexpf(1.f, 31 - max(f, -90));
                 // B_R = W fx / sa stays below 2^15 in FP16
                 if (FP16 && wmax > 0.f) {
-                    const float lim = 30000.f * sc.sa / wmax;
+                    const float lim = 30000.f * sa / wmax;
                     while (fx > lim) fx *= 0.5f;
                 }
             }
             rsc[0] = fx;
-            rsc[1] = fx / (sc.sa * p.wscale);
+            rsc[1] = fx / (sa * p.wscale);
             rsc[2] = 1.f / fx;
         }
         __syncthreads();
         const float bscale_r = rsc[1];
-#pragma unroll 1
-        for (int piece = 0; piece < NW; ++piece) {
-            const uint16_t* wsrc = p.wrow + (size_t)piece * P * P;
-            uint8_t* dst = sB + piece * b_piece;
-            for (int i = tid; i < KR * P; i += RP_THREADS) {
-                const int e = i / P, nn = i - (i / P) * P;
-                const uint16_t r = rsl[e];
-                uint16_t v = 0;
-                if (r != 0xFFFFu) {
-                    v = scale16<FP16>(__ldg(wsrc + (size_t)(r & 0x7FFFu) * P + nn), bscale_r);
-                    v ^= (uint16_t)(r & 0x8000u);   // exact negation
+        // B_R[s][e] = sgn_e W[slot e][s] bscale (NW pieces, canonical K-major layout
+        // without swizzle); the diagonal column from w_R in FP64
+        for (int i = tid; i < KR * P; i += RP_THREADS) {
+            const int e = i / P, nn = i - (i / P) * P;
+            const uint16_t r = rsl[e];
+            uint16_t v[NW];
+            if (r == 0xFFFEu) {
+                split16<FP16, NW>(wdg[nn] * (double)p.wscale * (double)bscale_r, v);
+            } else {
+#pragma unroll
+                for (int j = 0; j < NW; ++j) {
+                    v[j] = 0;
+                    if (r != 0xFFFFu) {
+                        v[j] = scale16<FP16>(__ldg(p.wrow + (size_t)j * P * P +
+                                                   (size_t)(r & 0x7FFFu) * P + nn), bscale_r);
+                        v[j] ^= (uint16_t)(r & 0x8000u);   // exact negation
+                    }
                 }
-                const uint32_t off = (uint32_t)(nn >> 3) * SBO_B + (uint32_t)(e >> 3) * 128u +
-                                     (uint32_t)(nn & 7) * 16u + (uint32_t)(e & 7) * 2u;
-                *reinterpret_cast<uint16_t*>(dst + off) = v;
             }
+            const uint32_t off = (uint32_t)(nn >> 3) * SBO_B + (uint32_t)(e >> 3) * 128u +
+                                 (uint32_t)(nn & 7) * 16u + (uint32_t)(e & 7) * 2u;
+#pragma unroll
+            for (int j = 0; j < NW; ++j) *reinterpret_cast<uint16_t*>(sB + j * b_piece + off) = v[j];
         }
         fence_proxy_async_smem();
         __syncthreads();
@@ -532,7 +556,7 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
                     // stage gt % nst is free once MMA(gt - nst) has completed
                     if (lane == 0)
                         ok = wait_phase(afree + gt % nst, (gt / nst - 1) & 1u, abort_flag, p.err,
-                                        RP_BACKOFF_NS);
+                                        p.wait_cycles, RP_BACKOFF_NS);
                     ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
                     if (!ok) break;
                 }
@@ -552,8 +576,8 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
             if (ok && ntiles > 0) publish(g + (uint32_t)ntiles - 1, false);
             cp_async_wait<0>();
         } else if (warp == RP_MMA_WARP) {
-            // ---- MMAs (one thread)
-            if (lane == 0) {
+            // ---- MMAs (one thread); with p.stall set nothing is issued or committed
+            if (lane == 0 && !p.stall) {
                 const int ksteps = KR / 16;
                 const uint64_t bdesc0 = smem_desc(sB_addr, 128u, SBO_B);
                 for (int t = 0; t < ntiles; ++t) {
@@ -561,10 +585,11 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
                     const uint32_t sg = gi % nst;
                     const uint32_t st = sA_addr + sg * 2u * a_piece;
                     const uint32_t d = tbase + (gi & 1u) * (uint32_t)P;
-                    if (!wait_phase(afull + sg, (gi / nst) & 1u, abort_flag, p.err, RP_BACKOFF_NS))
+                    if (!wait_phase(afull + sg, (gi / nst) & 1u, abort_flag, p.err, p.wait_cycles,
+                                    RP_BACKOFF_NS))
                         break;
                     if (gi >= 2 && !wait_phase(dfree + (gi & 1u), ((gi >> 1) - 1) & 1u,
-                                               abort_flag, p.err, RP_BACKOFF_NS))
+                                               abort_flag, p.err, p.wait_cycles, RP_BACKOFF_NS))
                         break;
                     tc_fence_after();
                     // descriptor address fields advance by (bytes >> 4): K step = 2 K-groups
@@ -621,11 +646,9 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
             };
             // one slot: sigma[tgt] += sign * round(D), unconditionally (an absent
             // slot's target is this lane's sink cell)
-            float dmax = 0.f;    // largest |D| this thread has seen in the row
             auto add = [&](uint32_t word, int half, uint32_t dbits) {
                 const uint32_t tg = half ? (word >> 16) & 0x7FFFu : word & 0x7FFFu;
                 const uint32_t sg = half ? (word & 0x80000000u) : (word << 16) & 0x80000000u;
-                dmax = fmaxf(dmax, fabsf(__uint_as_float(dbits)));
                 const int q = __float2int_rn(__uint_as_float(dbits ^ sg));
                 atomicAdd(srow + tg, q);
             };
@@ -634,7 +657,8 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
             for (int t = 0; t < ntiles && ok; ++t) {
                 const uint32_t gt = g + (uint32_t)t;
                 if (lane == 0)
-                    ok = wait_phase(dfull + (gt & 1u), (gt >> 1) & 1u, abort_flag, p.err);
+                    ok = wait_phase(dfull + (gt & 1u), (gt >> 1) & 1u, abort_flag, p.err,
+                                    p.wait_cycles);
                 ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
                 if (!ok) break;
                 tc_fence_after();
@@ -682,19 +706,11 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
                     }
                 }
             }
-            if (dmax >= dlimit) *range_flag = 1;
         }
         g += (uint32_t)ntiles;
         __syncthreads();
         if (*abort_flag) break;
-        if (*range_flag && p.flagged) {
-            // a term may have pushed a row sum past 32 bits: the row is redone at
-            // the a-priori scale by the following launch
-            if (tid == 0) p.flagged[atomicAdd(p.nflagged, 1)] = (int)ir;
-        } else {
-            for (int64_t j = tid; j < Nc; j += RP_THREADS)
-                p.Y[ir * Nc + j] = (float)srow[j] * rsc[2];
-        }
+        for (int64_t j = tid; j < Nc; j += RP_THREADS) p.Y[ir * Nc + j] = (float)srow[j] * rsc[2];
         __syncthreads();
     }
     tc_fence_before();
@@ -740,7 +756,9 @@ __global__ void k_wimg(const double* __restrict__ eri, int n, int P, int NS, int
         int pi, qi, po, qo;
         slot_pair(si, pi, qi);
         slot_pair(so, po, qo);
-        w = eri[(((int64_t)pi * n + qi) * n + po) * n + qo];
+        // (pp|qq) with both excitations diagonal only ever multiplies a determinant
+        // into itself: that part of the diagonal of H is added exactly elsewhere
+        if (!(pi == qi && po == qo)) w = eri[(((int64_t)pi * n + qi) * n + po) * n + qo];
     }
     w *= wscale;
     double rest = w;
@@ -784,14 +802,39 @@ __global__ void k_slot_table(const int32_t* __restrict__ tgt, const uint16_t* __
         (uint16_t)(tgt[i] | (sgn[i] < 0 ? 0x8000 : 0));
 }
 
-// row-string slot table: entry e of string r -> slot({p,q}) | (sgn < 0) << 15
-__global__ void k_row_slots(const uint16_t* __restrict__ pq, const int8_t* __restrict__ sgn,
-                            int64_t count, int n, uint16_t* __restrict__ out) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= count) return;
-    int a = pq[i] / n, b = pq[i] % n;
-    if (a > b) { int t = a; a = b; b = t; }
-    out[i] = (uint16_t)((b * (b + 1) / 2 + a) | (sgn[i] < 0 ? 0x8000 : 0));
+// row-string tables of the off-diagonal entries (p != q), in table order: target
+// and slot({p,q}) | (sgn < 0) << 15; one thread per string
+__global__ void k_row_offdiag(const int32_t* __restrict__ tgt, const uint16_t* __restrict__ pq,
+                              const int8_t* __restrict__ sgn, int64_t ns, int nexc, int noff,
+                              int n, int32_t* __restrict__ otgt, uint16_t* __restrict__ oslot) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= ns) return;
+    int k = 0;
+    for (int e = 0; e < nexc; ++e) {
+        const int64_t i = r * nexc + e;
+        int a = pq[i] / n, b = pq[i] % n;
+        if (a == b) continue;
+        if (a > b) { int t = a; a = b; b = t; }
+        otgt[r * noff + k] = tgt[i];
+        oslot[r * noff + k] = (uint16_t)((b * (b + 1) / 2 + a) | (sgn[i] < 0 ? 0x8000 : 0));
+        ++k;
+    }
+}
+
+// wd[q][s] = W[qq][s] = (qq|pr) for slot s = {p, r}, FP64 unscaled; zero for the
+// diagonal slots (p == r), whose part of the diagonal of H is added exactly elsewhere
+__global__ void k_wdiag(const double* __restrict__ eri, int n, int P, int NS,
+                        double* __restrict__ wd) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * P) return;
+    const int q = idx / P, so = idx % P;
+    double w = 0.0;
+    if (so < NS) {
+        int po, qo;
+        slot_pair(so, po, qo);
+        if (po != qo) w = eri[(((int64_t)q * n + q) * n + po) * n + qo];
+    }
+    wd[idx] = w;
 }
 
 // x [R][Cn] -> hi/lo BF16 pieces [R][pitch] (BF16 needs no scale); zero padding
@@ -817,12 +860,17 @@ uint32_t tmem_cols(int P) {
 
 size_t rowpass_smem(int P, int NW, int KR, int64_t Nc, int nst) {
     return (size_t)2 * nst * KR * 256 + (size_t)2 * NW * P * KR + 4 * (size_t)(Nc + RP_SINK) + 16 +
-           10 * RP_MAXK + 16 + 4 * RP_MAXK + 24 + 16 + 10 * 8 + 16;
+           10 * RP_MAXK + 16 + 4 * RP_MAXK + 24 + 16 + 8 * (size_t)P + 16 + 10 * 8 + 16;
 }
+
+// W in RP_NW 16-bit pieces (2: ~2^-22 relative per (pq|rs); 3: ~2^-33, a fourth
+// MMA pass and 50 % more shared memory for B_R, which leaves room for two A
+// stages only)
+constexpr int RP_NW = 2;
 
 template <int P>
 void* rowpass_fn(bool fp16) {
-    return fp16 ? (void*)k_rowpass<P, true, 2> : (void*)k_rowpass<P, false, 2>;
+    return fp16 ? (void*)k_rowpass<P, true, RP_NW> : (void*)k_rowpass<P, false, RP_NW>;
 }
 
 void* rowpass_kernel(int P, bool fp16) {
@@ -843,8 +891,8 @@ void* rowpass_kernel(int P, bool fp16) {
 }  // namespace
 
 void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
-                   const double* d_eri, int norb, double wmax, double wcolsum, bool use_fp16,
-                   cudaStream_t st) {
+                   const double* d_eri, const float2* d_diag, int norb, double wmax,
+                   double wcolsum, bool use_fp16, cudaStream_t st) {
     ta = &A;
     tb = &B;
     n = norb;
@@ -854,11 +902,15 @@ void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
     nsb = B.ns;
     dim = nsa * nsb;
     fp16 = use_fp16;
-    nw = 2;
+    nw = RP_NW;
     kernel = rowpass_kernel(P, fp16);
-    // at least one K step: a row without entries (no alpha electrons) then multiplies
-    // padding (B_R = 0) and D is exactly zero instead of never written
-    KR = A.nexc > 0 ? ((A.nexc + 15) / 16) * 16 : 16;
+    // off-diagonal entries of a row string, m (n - m), and one column for its m
+    // diagonal entries; at least one K step, so that a row without any (no alpha
+    // electrons) multiplies padding (B_R = 0) and D is exactly zero instead of
+    // never written
+    noff = A.m * (n - A.m);
+    ndiag = A.m > 0 ? 1 : 0;
+    KR = noff + ndiag > 0 ? ((noff + ndiag + 15) / 16) * 16 : 16;
     // 15-bit targets: every string index and sink cell (ns + 31) below 2^15
     if (!kernel || KR > RP_MAXK || A.ns > 32768 - RP_SINK || B.ns > 32768 - RP_SINK)
         KPM_THROW(KPM_EUNSUPPORTED, "tensor-core sigma supports up to 16 orbitals");
@@ -869,7 +921,6 @@ void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
     if (prop.major != 10)
         KPM_THROW(KPM_EUNSUPPORTED, "tensor-core sigma needs a Blackwell (sm_10x) GPU");
     nsm = prop.multiProcessorCount;
-    gbound = (float)(wcolsum * (1.0 + 1e-6));
     int64_t ncmax = nsa > nsb ? nsa : nsb;
     // three A stages where they fit (the copies of a tile then have two MMA
     // durations to land), else two
@@ -920,20 +971,24 @@ void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
     };
     build_slots(B, slot_b);
     {
-        const int64_t ne = A.ns * (int64_t)A.nexc;
-        rslot_a.alloc((size_t)(ne > 0 ? ne : 1) * sizeof(uint16_t));
-        if (ne > 0) {
-            k_row_slots<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
-                A.pq.as<uint16_t>(), A.sgn.as<int8_t>(), ne, n, rslot_a.as<uint16_t>());
+        const int64_t no = A.ns * (int64_t)noff;
+        rslot_a.alloc((size_t)(no > 0 ? no : 1) * sizeof(uint16_t));
+        rtgt_a.alloc((size_t)(no > 0 ? no : 1) * sizeof(int32_t));
+        if (no > 0) {
+            k_row_offdiag<<<(unsigned)((A.ns + 127) / 128), 128, 0, st>>>(
+                A.tgt.as<int32_t>(), A.pq.as<uint16_t>(), A.sgn.as<int8_t>(), A.ns, A.nexc, noff,
+                n, rtgt_a.as<int32_t>(), rslot_a.as<uint16_t>());
             KPM_LAUNCHED();
         }
+        wdiag.alloc((size_t)n * P * sizeof(double));
+        k_wdiag<<<(n * P + 255) / 256, 256, 0, st>>>(d_eri, n, P, NS, wdiag.as<double>());
+        KPM_LAUNCHED();
     }
     err.alloc(sizeof(int));
     amax.alloc(2 * sizeof(unsigned));
-    flagged.alloc((size_t)(nsa > 0 ? nsa : 1) * sizeof(int));
-    nflag.alloc(sizeof(int));
     KPM_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
     dense.init(A, B, &A == &B, err.as<int>(), st);
+    dense.diag_full = d_diag;
     dense.autotune(st);
 }
 
@@ -966,25 +1021,16 @@ void TcSigma::apply(const float* x, float* y, int ncol, cudaStream_t st) {
             xh = xbh.as<uint16_t>();
             xl = xbl.as<uint16_t>();
         }
-        // opposite-spin part: rows alpha, columns beta; writes Y.  First pass at a
-        // fixed-point scale 2^RP_SHIFT finer than the a-priori one, with a range
-        // check per row; second pass redoes the rows that failed it at the a-priori
-        // scale (its row count is read on the device: no synchronisation).
-        KPM_CUDA(cudaMemsetAsync(nflag.p, 0, sizeof(int), st));
+        // opposite-spin part: rows alpha, columns beta; writes Y
         RowPass p1{xh, xl, xp, Y, nsa, nsb, slot_b.as<uint4>(),
-                   ta->tgt.as<int32_t>(), rslot_a.as<uint16_t>(), ta->nexc, KR,
-                   wimg.as<uint16_t>(), nc, am, rowmax.as<float>(), wscale, gbound, tb->nexc, NS,
-                   nst, RP_SHIFT,
-                   nullptr, nullptr, flagged.as<int>(), nflag.as<int>(), err.as<int>()};
-        RowPass p2 = p1;
-        p2.shift = 0;
-        p2.rows = flagged.as<int>();
-        p2.nrows = nflag.as<int>();
-        p2.flagged = nullptr;
-        p2.nflagged = nullptr;
+                   rtgt_a.as<int32_t>(), rslot_a.as<uint16_t>(), noff, ndiag, KR,
+                   ta->masks.as<uint32_t>(), wdiag.as<double>(),
+                   wimg.as<uint16_t>(), nc, am, rowmax.as<float>(), wscale, tb->nexc, NS, nst,
+                   err.as<int>(), stall_next ? STALL_WAIT_CYCLES : WAIT_CYCLES,
+                   stall_next ? 1 : 0};
+        stall_next = false;
         int g1 = (int)(nsa < nsm ? nsa : nsm);
         void* args1[] = {&p1};
-        void* args2[] = {&p2};
         if (prof) {
             if ((int)ev.size() < ev_used + 2) {
                 cudaEvent_t e0, e1;
@@ -996,8 +1042,6 @@ void TcSigma::apply(const float* x, float* y, int ncol, cudaStream_t st) {
             KPM_CUDA(cudaEventRecord(ev[ev_used], st));
         }
         KPM_CUDA(cudaLaunchKernel(kernel, dim3(g1), dim3(RP_THREADS), args1, smem_bytes, st));
-        KPM_LAUNCHED();
-        KPM_CUDA(cudaLaunchKernel(kernel, dim3(g1), dim3(RP_THREADS), args2, smem_bytes, st));
         KPM_LAUNCHED();
         if (prof) {
             KPM_CUDA(cudaEventRecord(ev[ev_used + 1], st));

@@ -11,33 +11,38 @@ namespace kpm {
 // tensor cores.  See sigma_tc.cu for the formulation.
 struct TcSigma {
     int n = 0, NS = 0, P = 0;     // orbitals, unordered pairs n(n+1)/2, padded N (output slots)
-    int KR = 0;                   // K of the row GEMM: row-string table entries rounded to 16
+    int KR = 0;                   // K of the row GEMM: noff + ndiag rounded up to 16
     int64_t nsa = 0, nsb = 0, dim = 0;
     int nsm = 0;                  // SMs of the device (persistent grid)
     bool fp16 = false;            // operand format: split FP16 (scaled) or split BF16
-    int nw = 2;                   // 16-bit pieces of W
+    int nw = 3;                   // 16-bit pieces of W
     float wscale = 1.0f;          // power-of-two scale of W in the image
-    float gbound = 0.0f;          // max over output slots of sum over input slots of |W|
     void* kernel = nullptr;       // k_rowpass instantiation for P
     const SpinTables* ta = nullptr;
     const SpinTables* tb = nullptr;
     DevBuf wimg;                  // W = (pq|rs) over slot pairs, split into 16-bit pieces
-    DevBuf rslot_a;               // uint16 [N_a][nexc_a] entry -> slot | sign << 15
+    int noff = 0;                 // off-diagonal table entries per alpha string, m (n - m)
+    int ndiag = 0;                // 1: one K column for the diagonal entries (m >= 1)
+    DevBuf rslot_a;               // uint16 [N_a][noff] off-diagonal entry -> slot | sign << 15
+    DevBuf rtgt_a;                // int32  [N_a][noff] off-diagonal entry -> target string
+    DevBuf wdiag;                 // double [n][P] W[qq][s] (diagonal slots zero)
     DevBuf xbh, xbl;              // BF16 pieces of x (KPM_MIXED_BF16; FP16 pieces live in dense)
     DevBuf slot_b;                // uint16 [P/8][N_b][8] pair-slot -> target | sign << 15 (N_b: none)
     DenseSS dense;                // same-spin parts (dense GEMMs with F_a, F_b)
     DevBuf err;                   // int error flag (1: a bounded wait ran out)
     DevBuf amax;                  // max |x| (float bits): operand scale, fixed-point range
     DevBuf rowmax;                // [N_a] max |x| per row: per-row fixed-point range of the row pass
-    DevBuf flagged, nflag;        // rows redone at the a-priori fixed-point scale, and their count
     int nst = 2;                  // A stages of the row pass (3 where shared memory allows)
+    bool stall_next = false;      // test of the bounded waits: the next row pass stalls (see
+                                  // kpm_test_rowpass_stall)
     size_t smem_bytes = 0;
 
     // wmax: max |W| over (pq|rs) and k_pq (host-computed), for the FP16 scale;
-    // wcolsum: max over output slots s of sum over input slots k of |W[k][s]|.
+    // wcolsum: max over output slots s of sum over input slots k of |W[k][s]|;
+    // d_diag: the exact diagonal H_II [N_a][N_b] (float hi, lo), kept by the caller.
     void init(const SpinTables& ta, const SpinTables& tb, const double* d_h1,
-              const double* d_eri, int n, double wmax, double wcolsum, bool use_fp16,
-              cudaStream_t st);
+              const double* d_eri, const float2* d_diag, int n, double wmax, double wcolsum,
+              bool use_fp16, cudaStream_t st);
     void apply(const float* x, float* y, int ncol, cudaStream_t st);
     // Reads and clears the device error flag (synchronises the stream).
     int check(cudaStream_t st);

@@ -13,11 +13,11 @@
 
 #include "common.cuh"
 
+// Scratch for the damped moments: 2 MiB per device, file scope, internal linkage.
+static __device__ __align__(256) double g_spectrum_scratch[KPM_SPECTRUM_STATIC_MAX_MOMENTS];
+
 namespace kpm {
 namespace {
-
-// Scratch for the damped moments: 2 MiB per device.
-__device__ __align__(256) double g_spectrum_scratch[KPM_SPECTRUM_STATIC_MAX_MOMENTS];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mutex;
@@ -25,7 +25,9 @@ double* g_scratch_addr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device.  In host code the
 // array's name is only a host-side stand-in, so the address is looked up once
-// per device with that device current and cached.
+// per device with that device current and cached.  A cudaDeviceReset destroys
+// the context that held the array; the cached address is then stale, so a
+// process that resets a device must not call kpm_spectrum_static on it again.
 double* scratch_address() {
     int dev = 0;
     KPM_CUDA(cudaGetDevice(&dev));
@@ -56,7 +58,7 @@ extern "C" kpm_status kpm_spectrum_static(const double* moments_dev, int nmoment
     try {
         if (!moments_dev || !omega_dev || !intensity_dev)
             KPM_THROW(KPM_EINVAL, "NULL argument");
-        if (nmoments < 1 || npoints < 1 || (kernel != 0 && kernel != 1))
+        if (nmoments < 1 || npoints < 1 || kernel < 0 || kernel > 2)
             KPM_THROW(KPM_EINVAL, "bad spectrum arguments");
         if (nmoments > KPM_SPECTRUM_STATIC_MAX_MOMENTS)
             KPM_THROW(KPM_EINVAL,

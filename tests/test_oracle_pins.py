@@ -409,6 +409,37 @@ def test_block_recursion_equals_column_recursion():
         assert np.abs(mb[c] - mc).max() < 1e-13 * mc[0]
 
 
+def test_lorentz_kernel_closed_form_and_sum_rule():
+    """Lorentz factors: g_0 = 1, strictly decreasing, g_{N-1} = sinh(lam/N)/sinh(lam);
+    its spectrum keeps the discrete sum rule and is non-negative for a delta."""
+    N, M, lam = 256, 1024, 4.0
+    g = kpm.lorentz(N, lam)
+    assert g[0] == 1.0 and np.all(np.diff(g) < 0) and g[-1] > 0
+    assert abs(g[-1] - np.sinh(lam / N) / np.sinh(lam)) < 1e-15
+    for x0 in (-0.9, 0.0, 0.73):
+        mu = np.cos(np.arange(N) * np.arccos(x0))
+        om, dens = kpm.spectrum(mu, 1.0, 0.0, M, kernel="lorentz", lam=lam)
+        th = np.arccos(om)
+        assert abs(np.pi / M * np.sum(np.sin(th) * dens) - 1.0) < 1e-12
+        assert dens.min() > -1e-12 * dens.max()
+        assert abs(om[np.argmax(dens)] - x0) < 2 * np.pi / N
+
+
+def test_cross_moments_eigenpairs_and_autocorrelation_8o():
+    """C_AB moments <0|A T_n B|0> (direct recursion) against the eigenpair sum, and
+    A = B against the doubling-identity autocorrelation moments."""
+    I, sc, H, E, U = _system8()
+    a, b = kpm.scale_from_bounds(E[0], E[-1])
+    psi0 = U[:, 0]
+    left = -sc.dipole(-I.dipole[0], psi0)        # A|0> with A = sum op E_pq, op = -d^x
+    right = -sc.dipole(-I.dipole[1], psi0)       # B|0>, op = -d^y
+    mc = kpm.moments_cross(sc.sigma, left, right, a, b, 128)
+    me = kpm.moments_cross_eigen(E, U, left, right, a, b, 128)
+    assert np.abs(mc - me).max() < 1e-11 * np.sqrt((left @ left) * (right @ right))
+    ma = kpm.moments_cross(sc.sigma, left, left, a, b, 128)
+    assert np.abs(ma - kpm.moments_recursion(sc.sigma, left, a, b, 128)).max() < 1e-11 * (left @ left)
+
+
 # ---------------------------------------------------------------- planted mistakes
 
 def test_planted_transposed_eri_is_caught():

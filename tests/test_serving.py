@@ -73,6 +73,38 @@ def test_served_request_matches_oracle(cases):
     assert r["t_total_s"] >= r["t_run_s"] >= 0.0
 
 
+def test_served_mixed_request_matches_oracle():
+    """A tensor-core (KPM_MIXED) request served beside another: 10 orbitals, the
+    oracle's ground state and energy (deflated recursion), 512 moments of the z
+    component, against the oracle's
+    FP64 recursion (moments within 1e-6 Omega_0) and its spectrum (relative L2
+    within 1e-4)."""
+    from paper_2506_07430_gb300 import Server
+    n, m = 10, 5
+    I = synthetic.integrals(n, m, m, 2506106)
+    sc = oracle.SlaterCondon(I.h1, I.eri, n, m, m)
+    sc.csr()
+    e0, psi0 = oracle.ground_state(sc.sigma, sc.dim)
+    a, b = okpm.scale_from_bounds(*oracle.spectral_bounds(sc.sigma, sc.dim))
+    N, M = 512, 1024
+    ref = okpm.moments_recursion(sc.sigma, sc.dipole(I.dipole[2], psi0), a, b, N)
+    other = synthetic.integrals(8, 4, 4, 2506101)
+    srv = Server(mem_budget_bytes=4 << 30, max_slots=2, steps_per_round=8, precision="mixed")
+    i_other = srv.submit(other.h1, other.eri, other.dipole, 8, 4, 4,
+                         synthetic.random_state(4900, 5), 0b111, 30.0, -10.0, 128, npoints=256)
+    rid = srv.submit(I.h1, I.eri, I.dipole, n, m, m, psi0, 0b100, a, b, N, npoints=M, e0=e0)
+    r = srv.wait(rid)
+    srv.wait(i_other, allow_ebounds=True)
+    srv.close()
+    err = np.abs(r["moments"][0] - ref).max() / ref[0]
+    om_r, it_r = okpm.spectrum(ref, a, b, M)
+    serr = np.linalg.norm(r["intensity"] - it_r) / np.linalg.norm(it_r)
+    print("served MIXED 10o: max |dOmega_n|/Omega_0 =", err, "spectrum rel L2 =", serr)
+    assert np.abs(r["omega"] - om_r).max() < 1e-12 * (abs(a) + abs(b))
+    assert err < 1e-6, err
+    assert serr < 1e-4, serr
+
+
 def test_admission_respects_memory_budget(cases):
     from paper_2506_07430_gb300 import Server
     big = [c for c in cases if c[0] == 10]
@@ -98,4 +130,33 @@ def test_cancel_and_timeout(cases):
         srv.wait(i1)
     r0 = srv.wait(i0)
     assert r0["status"] == 0
+    srv.close()
+
+
+def test_injected_advance_failure_fails_only_that_request(cases):
+    """Host-side fault injection: one request's advance reports a failure.  That
+    request alone is finished with the status (kpm_server_wait returns it), its
+    slot and budget are released, and the requests beside it give the same
+    results as alone."""
+    from paper_2506_07430_gb300 import KPMError, Server
+    from paper_2506_07430_gb300._lib import KPM_ECUDA
+    srv = Server(mem_budget_bytes=4 << 30, max_slots=3, steps_per_round=8, precision="fp64")
+    alone = [srv.wait(_submit(srv, c)) for c in cases[:3]]
+    ids = []
+    for i, c in enumerate(cases[:3]):
+        ids.append(_submit(srv, c))
+        if i == 1:
+            srv.inject_failure(ids[1], KPM_ECUDA)   # before its set-up has finished
+    with pytest.raises(KPMError, match="KPM_ECUDA"):
+        srv.wait(ids[1])
+    for i in (0, 2):
+        r = srv.wait(ids[i])
+        assert r["status"] == 0
+        assert np.array_equal(r["moments"], alone[i]["moments"])
+        assert np.array_equal(r["intensity"], alone[i]["intensity"])
+    st = srv.stats()
+    assert st["mem_used"] == 0 and st["resident"] == 0 and st["queued"] == 0, st
+    # the server keeps serving after the failure
+    r = srv.wait(_submit(srv, cases[1]))
+    assert np.array_equal(r["moments"], alone[1]["moments"])
     srv.close()

@@ -51,6 +51,37 @@ def test_static_spectrum_matches_allocating_entry_point():
         assert np.linalg.norm(it - it_ref) <= TOL * np.linalg.norm(it_ref), call
 
 
+def test_static_spectrum_leaves_device_memory_unchanged():
+    """After a first call (which loads the kernels and looks up the array's
+    address), further calls leave the device's free memory exactly as it was:
+    nothing is allocated, the scratch is the library's fixed array."""
+    import torch
+
+    from paper_2506_07430_gb300 import load_library
+
+    lib = load_library()
+    stream = torch.cuda.current_stream()
+    N, M = 4096, 1024
+    mu_d = torch.tensor(_case(3, N), dtype=torch.float64, device="cuda")
+    om_d = torch.empty(M, dtype=torch.float64, device="cuda")
+    it_d = torch.empty(M, dtype=torch.float64, device="cuda")
+
+    def call():
+        st = lib.kpm_spectrum_static(mu_d.data_ptr(), N, 1.5, 0.5, M, 1, om_d.data_ptr(),
+                                     it_d.data_ptr(), ctypes.c_void_p(stream.cuda_stream))
+        assert st == 0, lib.kpm_last_error(None)
+
+    call()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    first = it_d.cpu().numpy()
+    for _ in range(20):
+        call()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert np.array_equal(it_d.cpu().numpy(), first)
+
+
 def test_static_spectrum_rejects_oversized_request():
     import torch
 
