@@ -146,6 +146,26 @@ kpm_status kpm_string_table(const kpm_ctx* ctx, int spin, uint32_t* masks, int32
 kpm_status kpm_sigma(kpm_ctx* ctx, const void* x, void* y, int ncol);
 
 /*
+ * kpm_sigma_pauli -- y = H x with H in the Jordan-Wigner Pauli-string form the
+ * paper maps the second-quantized Hamiltonian to (Methods, "Mapping fermionic
+ * Hamiltonians to the qubits"): qubits are the spin orbitals in this library's
+ * determinant order (alpha 0..n-1, beta n..2n-1), a+_q = (X_q - i Y_q)/2 Z_{<q},
+ * and H becomes a real sum of strings c X^x Z^z (built on the host at the first
+ * call from the context's integrals; equal strings merged).  The kernel pulls
+ * every output determinant's terms over the strings' flip masks (FP64 sums; x and
+ * y in the context's vector type; FP64 or FP32 contexts, and tensor-core contexts
+ * with FP32 vectors).  It is the same H as kpm_sigma, for comparison with the
+ * paper's representation; its cost grows with the number of strings (O(n^4)), so
+ * it is meant for small systems.  Asynchronous after the first call.
+ * Errors: KPM_EINVAL (NULL, ncol outside 1..64, x == y).
+ */
+kpm_status kpm_sigma_pauli(kpm_ctx* ctx, const void* x, void* y, int ncol);
+
+/* Number of Pauli strings of kpm_sigma_pauli's H and of their distinct flip
+ * masks (builds the form if needed; synchronous). */
+kpm_status kpm_pauli_terms(kpm_ctx* ctx, int64_t* nterms, int* ngroups);
+
+/*
  * kpm_apply_dipole -- y = mu^comp psi (comp 0,1,2 = x,y,z); psi FP64 device
  * [dim], y device [dim] in the context precision.  Asynchronous.
  * Paper: Methods, dipole operator mu = -sum_pq d_pq (c+_up c_up + c+_dn c_dn).

@@ -28,6 +28,8 @@ SIGNATURES = {
     "kpm_nexc": (_I, [_P, _I]),
     "kpm_string_table": (_I, [_P, _I, _P, _P, _P, _P]),
     "kpm_sigma": (_I, [_P, _P, _P, _I]),
+    "kpm_sigma_pauli": (_I, [_P, _P, _P, _I]),
+    "kpm_pauli_terms": (_I, [_P, _P, _P]),
     "kpm_apply_dipole": (_I, [_P, _I, _P, _P]),
     "kpm_bounds": (_I, [_P, _I, _U64, _P, _P]),
     "kpm_scale": (None, [_D, _D, _D, _P, _P]),
@@ -198,6 +200,21 @@ class KPM:
         _check(self._lib().kpm_sigma(self._h, _dev_ptr(x, self.vdtype), _dev_ptr(y, self.vdtype),
                                      ncol), self._h)
         return y
+
+    def sigma_pauli(self, x, y=None):
+        """y = H x with H as Jordan-Wigner Pauli strings (kpm_sigma_pauli)."""
+        ncol = 1 if x.dim() == 1 else x.shape[0]
+        if y is None:
+            y = x.new_empty(x.shape)
+        _check(self._lib().kpm_sigma_pauli(self._h, _dev_ptr(x, self.vdtype),
+                                           _dev_ptr(y, self.vdtype), ncol), self._h)
+        return y
+
+    def pauli_terms(self):
+        """(number of Pauli strings, number of distinct flip masks)."""
+        nt, ng = ctypes.c_int64(), ctypes.c_int()
+        _check(self._lib().kpm_pauli_terms(self._h, ctypes.byref(nt), ctypes.byref(ng)), self._h)
+        return nt.value, ng.value
 
     def apply_dipole(self, comp: int, psi, y=None):
         import torch

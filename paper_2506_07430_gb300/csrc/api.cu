@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "pauli.cuh"
 #include "sigma_tc.cuh"
 
 using namespace kpm;
@@ -29,6 +30,7 @@ struct kpm_ctx {
     SpinTables ta, tb_own;
     SpinTables* tb = nullptr;
     std::unique_ptr<TcSigma> tc;  // tensor-core sigma (KPM_MIXED)
+    std::unique_ptr<PauliH> pauli;  // Pauli-string form of H (built on first use)
 
     // recursion state
     int rec_ncol = 0, rec_steps = 0, rec_max_steps = 0;
@@ -666,6 +668,42 @@ kpm_status kpm_sigma(kpm_ctx* ctx, const void* x, void* y, int ncol) {
         if (x == y) KPM_THROW(KPM_EINVAL, "x and y must not alias");
         DeviceGuard g(ctx->device);
         sigma_dispatch(ctx, x, y, ncol);
+    });
+}
+
+// builds the Pauli-string form of H from the context's integrals on first use
+static PauliH& pauli_of(kpm_ctx* ctx) {
+    if (!ctx->pauli) {
+        const int n = ctx->n;
+        std::vector<double> h1((size_t)n * n), eri((size_t)n * n * n * n);
+        KPM_CUDA(cudaStreamSynchronize(ctx->st));
+        KPM_CUDA(cudaMemcpy(h1.data(), ctx->d_h1.p, h1.size() * 8, cudaMemcpyDeviceToHost));
+        KPM_CUDA(cudaMemcpy(eri.data(), ctx->d_eri.p, eri.size() * 8, cudaMemcpyDeviceToHost));
+        auto p = std::make_unique<PauliH>();
+        p->build(h1.data(), eri.data(), n, ctx->na, ctx->nb);
+        ctx->pauli = std::move(p);
+    }
+    return *ctx->pauli;
+}
+
+kpm_status kpm_sigma_pauli(kpm_ctx* ctx, const void* x, void* y, int ncol) {
+    if (!ctx) { g_err = "NULL context"; return KPM_EINVAL; }
+    return guarded(ctx, [&] {
+        if (!x || !y || ncol < 1 || ncol > 64) KPM_THROW(KPM_EINVAL, "bad sigma arguments");
+        if (x == y) KPM_THROW(KPM_EINVAL, "x and y must not alias");
+        DeviceGuard g(ctx->device);
+        PauliH& ph = pauli_of(ctx);
+        ph.apply(ctx->ta, *ctx->tb, x, y, ncol, ctx->prec == KPM_FP64, ctx->st);
+    });
+}
+
+kpm_status kpm_pauli_terms(kpm_ctx* ctx, int64_t* nterms, int* ngroups) {
+    if (!ctx) { g_err = "NULL context"; return KPM_EINVAL; }
+    return guarded(ctx, [&] {
+        DeviceGuard g(ctx->device);
+        PauliH& ph = pauli_of(ctx);
+        if (nterms) *nterms = ph.nterms;
+        if (ngroups) *ngroups = ph.ngroups;
     });
 }
 

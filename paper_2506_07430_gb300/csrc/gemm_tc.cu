@@ -43,7 +43,14 @@ constexpr int GM_EPI_WARPS = 8;               // 2 per TMEM lane quadrant, 128 c
 constexpr int GM_TMA_WARP = GM_EPI_WARPS;       // producer (one thread)
 constexpr int GM_MMA_WARP = GM_EPI_WARPS + 1;   // MMA issue (one thread)
 constexpr int GM_THREADS = 32 * (GM_EPI_WARPS + 2);
-constexpr int GM_CHUNKS = 24;                   // target number of accumulation chunks over K
+// Accumulation chunks over K.  The tensor cores' FP32 accumulation rounds each
+// addition into the accumulator toward zero (it shrinks every running sum by up
+// to one unit in the last place), a bias that grows with the number of MMAs
+// accumulated and would act as a fixed scaling of H; restarting the accumulator
+// every k-block (12 MMAs, the 8 small correction products first, so that their
+// additions truncate at their own small scale) and adding the chunks into FP32
+// running sums in registers (round to nearest) keeps it near 4 units of 2^-24.
+constexpr int GM_CK = 1;                        // k-blocks per accumulation chunk
 // poll interval of the epilogue warps' waits (a chunk accumulates for microseconds)
 #ifndef GM_BACKOFF_NS
 #define GM_BACKOFF_NS 256
@@ -211,7 +218,7 @@ k_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensor
     const int m0 = (first_m + (b % gsize) % gm) * GM_BM;
     const int n0 = ((b % gsize) / gm) * GM_BN;
     const int nk = (g.K + GM_BK - 1) / GM_BK;
-    const int ck = max(2, (nk + GM_CHUNKS - 1) / GM_CHUNKS);   // k-blocks per chunk
+    const int ck = GM_CK;                                      // k-blocks per chunk
     const int nchunk = (nk + ck - 1) / ck;
 
     if (tid == 0) {
@@ -282,13 +289,19 @@ k_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensor
                     const uint32_t st = su32(smem + s * STAGE_BYTES);
                     const uint32_t a0 = st, a1 = st + A_BYTES, b0 = st + 2 * A_BYTES,
                                    b1 = st + 2 * A_BYTES + B_BYTES;
+                    // correction products (lo x hi, hi x lo) first, while the running
+                    // sum is small, then the main products (hi x hi)
 #pragma unroll
                     for (int j = 0; j < GM_BK / 16; ++j) {
                         const uint32_t off = j * 32;  // 16 FP16 = 32 bytes along K in the atom row
                         const uint32_t acc0 = (kb != c * ck || j != 0) ? 1u : 0u;
-                        mma_ss(d, sw128_desc(a0 + off), sw128_desc(b0 + off), idesc, acc0);
-                        mma_ss(d, sw128_desc(a1 + off), sw128_desc(b0 + off), idesc, 1);
+                        mma_ss(d, sw128_desc(a1 + off), sw128_desc(b0 + off), idesc, acc0);
                         mma_ss(d, sw128_desc(a0 + off), sw128_desc(b1 + off), idesc, 1);
+                    }
+#pragma unroll
+                    for (int j = 0; j < GM_BK / 16; ++j) {
+                        const uint32_t off = j * 32;
+                        mma_ss(d, sw128_desc(a0 + off), sw128_desc(b0 + off), idesc, 1);
                     }
                     mma_commit_(&empty[s]);
                 }

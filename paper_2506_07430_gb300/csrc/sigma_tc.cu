@@ -173,7 +173,10 @@ struct RowPass {
 };
 
 constexpr int RP_SCATTER_WARPS = 16;         // 4 per TMEM lane quadrant
-constexpr int RP_COPY_WARPS = 3;             // cp.async producers (warps 16-18)
+#ifndef RP_COPY_WARPS_N
+#define RP_COPY_WARPS_N 3
+#endif
+constexpr int RP_COPY_WARPS = RP_COPY_WARPS_N;   // cp.async producers (warps 16 ...)
 constexpr int RP_MMA_WARP = RP_SCATTER_WARPS + RP_COPY_WARPS;   // MMA issue (one thread)
 constexpr int RP_WARPS = RP_SCATTER_WARPS + RP_COPY_WARPS + 1;
 constexpr int RP_THREADS = 32 * RP_WARPS;
@@ -184,9 +187,13 @@ static_assert(RP_COPY_WARPS * 32 >= RP_MAXK, "one copy lane per entry (L2 prefet
 // lanes of a warp (32 consecutive J) sink into 32 different banks
 constexpr int RP_SINK = 32;
 // poll interval of the copy and MMA warps' waits (the MMA of tile t + 1 has
-// about one scatter duration of slack, microseconds)
+// about one scatter duration of slack, microseconds), and of the scatter warps'
+// wait for D
 #ifndef RP_BACKOFF_NS
 #define RP_BACKOFF_NS 256
+#endif
+#ifndef RP_SCATTER_BACKOFF_NS
+#define RP_SCATTER_BACKOFF_NS 0
 #endif
 // the copy warps prefetch the A rows of tile t + RP_PREFETCH into L2 when they
 // copy tile t (a quarter of the gathered segments miss L2; 0: no prefetch)
@@ -596,17 +603,21 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
                     // of A (2 * A_LBO bytes) and 256 bytes of B
                     const uint64_t a_hi = smem_desc(st, A_LBO, A_SBO);
                     const uint64_t a_lo = a_hi + (a_piece >> 4);
+                    // the small correction products first (A_lo B_0, then A_hi B_j for
+                    // j >= 1), the main product A_hi B_0 last: the accumulator rounds
+                    // each addition toward zero, so each addition should land on a
+                    // running sum as small as possible (see GM_CK in gemm_tc.cu)
 #pragma unroll
-                    for (int pass = 0; pass < NW + 1; ++pass) {
-                        // pass 0: A_hi B_0, pass 1: A_lo B_0, pass j+1 (j >= 1): A_hi B_j
-                        const uint64_t ad0 = pass == 1 ? a_lo : a_hi;
-                        const uint64_t bd0 = bdesc0 + (uint64_t)((pass <= 1 ? 0 : pass - 1) *
+                    for (int q = 0; q < NW + 1; ++q) {
+                        // q = 0: A_lo B_0; 1 <= q < NW: A_hi B_q; q = NW: A_hi B_0
+                        const uint64_t ad0 = q == 0 ? a_lo : a_hi;
+                        const uint64_t bd0 = bdesc0 + (uint64_t)((q == 0 || q == NW ? 0 : q) *
                                                                  (b_piece >> 4));
 #pragma unroll
                         for (int j = 0; j < RP_MAXK / 16; ++j) {
                             if (j < ksteps)
                                 mma_ss(d, ad0 + (uint64_t)(j * (2 * A_LBO >> 4)),
-                                       bd0 + (uint64_t)(j * 16), idesc, (pass | j) != 0);
+                                       bd0 + (uint64_t)(j * 16), idesc, (q | j) != 0);
                         }
                     }
                     mma_commit(afree + sg);
@@ -658,7 +669,7 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
                 const uint32_t gt = g + (uint32_t)t;
                 if (lane == 0)
                     ok = wait_phase(dfull + (gt & 1u), (gt >> 1) & 1u, abort_flag, p.err,
-                                    p.wait_cycles);
+                                    p.wait_cycles, RP_SCATTER_BACKOFF_NS);
                 ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
                 if (!ok) break;
                 tc_fence_after();
