@@ -193,7 +193,7 @@ constexpr int RP_SINK = 32;
 #define RP_BACKOFF_NS 256
 #endif
 #ifndef RP_SCATTER_BACKOFF_NS
-#define RP_SCATTER_BACKOFF_NS 0
+#define RP_SCATTER_BACKOFF_NS 64
 #endif
 // the copy warps prefetch the A rows of tile t + RP_PREFETCH into L2 when they
 // copy tile t (a quarter of the gathered segments miss L2; 0: no prefetch)
