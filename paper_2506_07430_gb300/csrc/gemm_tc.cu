@@ -4,9 +4,11 @@
 //   sigma_bb[I_a][I_b] = sum_J F_b[I_b][J] C[I_a][J]      (beta string Hamiltonian)
 //   sigma_aa[I_a][I_b] = sum_J F_a[I_a][J] C[J][I_b]      (alpha string Hamiltonian)
 // F_s is the Slater-Condon matrix of one spin's strings (tables.cu), symmetric,
-// with about 6.6 % nonzeros at 16 orbitals and no useful block sparsity at
-// 128 x 128 tiles (83 % of the tiles hold a nonzero), so both products run as
-// dense GEMMs: out[m][n] = sum_k A[m][k] B[n][k] with both operands K-major,
+// with about 6.6 % nonzeros at 16 orbitals spread over most tiles (83 % of the
+// 128 x 128 tiles hold a nonzero), so both products run as dense GEMMs that skip
+// only the all-zero k-blocks of the matrix operand's tile (22 % of the 128 x 64
+// blocks of F_b, 15 % of the 256 x 64 blocks of F_a at 16 orbitals):
+// out[m][n] = sum_k A[m][k] B[n][k] with both operands K-major,
 //   beta:  A = F_b (m = I_b, k = J),      B = C (n = I_a, k = J)
 //   alpha: A = C^T (m = I_b, k = J),      B = F_a (n = I_a, k = J)
 // and in both cases the epilogue adds out[m][n] into y[n * ldy + m], so the 32
@@ -32,6 +34,7 @@
 #include <array>
 #include <map>
 #include <mutex>
+#include <vector>
 
 #include "gemm_tc.cuh"
 
@@ -160,6 +163,13 @@ struct GemmArgs {
     const float2* dfull;
     int* err;
     int group_m;               // row tiles per rasterisation group (tuned; see DenseSS::autotune)
+    // k-blocks holding a nonzero of the matrix operand, per tile of that operand (CSR:
+    // kbl[kbs[t] .. kbs[t + 1]) ascending); the tile is the row tile m0 / GM_BM when
+    // kb_by_n == 0 (matrix in A) or the column tile n0 / GM_BN (matrix in B).  A
+    // skipped k-block only adds zero products, so the sums are unchanged.  Null: all.
+    const int* kbs;
+    const int* kbl;
+    int kb_by_n;
 };
 
 // bounded wait that also gives up when another role has aborted; roles off the
@@ -217,7 +227,15 @@ k_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensor
     const int gm = min(nM - first_m, GROUP_M);
     const int m0 = (first_m + (b % gsize) % gm) * GM_BM;
     const int n0 = ((b % gsize) / gm) * GM_BN;
-    const int nk = (g.K + GM_BK - 1) / GM_BK;
+    // k-blocks this tile visits: all of K, or the list of blocks where the matrix
+    // operand's tile has a nonzero
+    int nk = (g.K + GM_BK - 1) / GM_BK;
+    const int* klist = nullptr;
+    if (g.kbs) {
+        const int t = g.kb_by_n ? n0 / GM_BN : m0 / GM_BM;
+        klist = g.kbl + g.kbs[t];
+        nk = g.kbs[t + 1] - g.kbs[t];
+    }
     const int ck = GM_CK;                                      // k-blocks per chunk
     const int nchunk = (nk + ck - 1) / ck;
 
@@ -259,7 +277,7 @@ k_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensor
                     break;
                 unsigned char* st = smem + s * STAGE_BYTES;
                 mbar_expect_tx(&full[s], STAGE_BYTES);
-                const int kx = kb * GM_BK;
+                const int kx = (klist ? klist[kb] : kb) * GM_BK;
                 tma_load_2d(su32(st), &mA0, kx, m0, &full[s]);
                 tma_load_2d(su32(st + A_BYTES), &mA1, kx, m0, &full[s]);
                 tma_load_2d(su32(st + 2 * A_BYTES), &mB0, kx, n0, &full[s]);
@@ -467,6 +485,17 @@ __global__ void k_zero_half(__half* p, int64_t n) {
         p[i] = __float2half(0.f);
 }
 
+// mark[(r / rows) * nkb + c / GM_BK] = 1 for every off-diagonal neighbour entry
+// (r, c): the k-blocks of each `rows`-row tile of the split matrix that hold a nonzero.
+__global__ void k_mark_blocks(const int32_t* __restrict__ fcol, int64_t ns, int nnbr, int rows,
+                              int64_t nkb, unsigned char* __restrict__ mark) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ns * (nnbr - 1)) return;
+    const int64_t t = 1 + i / ns, r = i % ns;
+    const int64_t c = fcol[t * ns + r];
+    mark[(r / rows) * nkb + c / GM_BK] = 1;
+}
+
 // diag[r] = F[r][r] (entry t = 0), as float hi + lo.
 __global__ void k_diag_pair(const double* __restrict__ fval, int64_t ns, float2* __restrict__ d) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -556,6 +585,39 @@ static void build_f(const SpinTables& T, double ws, DevBuf& hi, DevBuf& lo, DevB
     KPM_LAUNCHED();
 }
 
+// Lists, per tile of `rows` rows of the split matrix of T, the k-blocks holding a
+// nonzero (CSR start[ntiles + 1] and list, both int32 on the device).
+static void block_lists(const SpinTables& T, int rows, DevBuf& start, DevBuf& list,
+                        int64_t* nonzero, int64_t* total, cudaStream_t st) {
+    const int64_t ntile = (T.ns + rows - 1) / rows, nkb = (T.ns + GM_BK - 1) / GM_BK;
+    DevBuf mark;
+    mark.alloc((size_t)(ntile * nkb));
+    KPM_CUDA(cudaMemsetAsync(mark.p, 0, mark.bytes, st));
+    const int64_t ne = T.ns * (int64_t)(T.nnbr - 1);
+    if (ne > 0) {
+        k_mark_blocks<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
+            T.fcol.as<int32_t>(), T.ns, T.nnbr, rows, nkb, mark.as<unsigned char>());
+        KPM_LAUNCHED();
+    }
+    std::vector<unsigned char> h((size_t)(ntile * nkb));
+    KPM_CUDA(cudaMemcpyAsync(h.data(), mark.p, h.size(), cudaMemcpyDeviceToHost, st));
+    KPM_CUDA(cudaStreamSynchronize(st));
+    std::vector<int> hs((size_t)ntile + 1, 0), hl;
+    for (int64_t t = 0; t < ntile; ++t) {
+        for (int64_t k = 0; k < nkb; ++k)
+            if (h[(size_t)(t * nkb + k)]) hl.push_back((int)k);
+        hs[(size_t)t + 1] = (int)hl.size();
+    }
+    if (hl.empty()) hl.push_back(0);  // keeps the list buffer non-empty
+    start.alloc(hs.size() * sizeof(int));
+    list.alloc(hl.size() * sizeof(int));
+    KPM_CUDA(cudaMemcpyAsync(start.p, hs.data(), start.bytes, cudaMemcpyHostToDevice, st));
+    KPM_CUDA(cudaMemcpyAsync(list.p, hl.data(), list.bytes, cudaMemcpyHostToDevice, st));
+    KPM_CUDA(cudaStreamSynchronize(st));
+    *nonzero = hs.back();
+    *total = ntile * nkb;
+}
+
 void DenseSS::init(const SpinTables& A, const SpinTables& B, bool same, int* err_flag,
                    cudaStream_t st) {
     na = A.ns;
@@ -580,6 +642,10 @@ void DenseSS::init(const SpinTables& A, const SpinTables& B, bool same, int* err
         fa_lo = &fa_lo_own;
         da = &da_own;
     }
+    // beta: F_b is the A operand (GM_BM-row tiles); alpha: F_a is the B operand
+    // (GM_BN-row tiles)
+    block_lists(B, GM_BM, kbs_b, kbl_b, &kb_nonzero[0], &kb_total[0], st);
+    block_lists(A, GM_BN, kbs_a, kbl_a, &kb_nonzero[1], &kb_total[1], st);
 }
 
 void DenseSS::split(const float* x, const float* amax, cudaStream_t st) {
@@ -597,7 +663,7 @@ void DenseSS::launch_beta(float* y, const float* amax, int group, cudaStream_t s
     CUtensorMap b0 = make_map(xh.as<__half>(), na, nb, xpitch, GM_BN);
     CUtensorMap b1 = make_map(xl.as<__half>(), na, nb, xpitch, GM_BN);
     GemmArgs g{(int)nb, (int)na, (int)nb, y, nb, 1.0f, amax, (float)wscale_b,
-               nullptr, nullptr, err, group};
+               nullptr, nullptr, err, group, kbs_b.as<int>(), kbl_b.as<int>(), 0};
     dim3 grid((unsigned)(((nb + GM_BM - 1) / GM_BM) * ((na + GM_BN - 1) / GM_BN)));
     k_gemm<<<grid, GM_THREADS, smem, st>>>(a0, a1, b0, b1, g);
     KPM_LAUNCHED();
@@ -612,7 +678,7 @@ void DenseSS::launch_alpha(const float* x, float* y, const float* amax, int grou
     CUtensorMap b0 = make_map(fa_hi->as<__half>(), na, na, pa, GM_BN);
     CUtensorMap b1 = make_map(fa_lo->as<__half>(), na, na, pa, GM_BN);
     GemmArgs g{(int)nb, (int)na, (int)na, y, nb, 1.0f, amax, (float)wscale_a,
-               diag, diag ? diag_full : nullptr, err, group};
+               diag, diag ? diag_full : nullptr, err, group, kbs_a.as<int>(), kbl_a.as<int>(), 1};
     dim3 grid((unsigned)(((nb + GM_BM - 1) / GM_BM) * ((na + GM_BN - 1) / GM_BN)));
     k_gemm<<<grid, GM_THREADS, smem, st>>>(a0, a1, b0, b1, g);
     KPM_LAUNCHED();

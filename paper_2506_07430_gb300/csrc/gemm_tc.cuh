@@ -19,6 +19,10 @@ struct DenseSS {
     int64_t xpitch = 0;                       // row pitch of xh/xl: N_b rounded up to 128
     DevBuf xh, xl, th, tl;                    // split copies of x and x^T
     DevBuf fmax;                              // scratch for max |F_off|
+    // per tile of the split matrix, the k-blocks that hold a nonzero (CSR; see
+    // block_lists): beta GEMM (F_b, 128-row tiles), alpha GEMM (F_a, 256-row tiles)
+    DevBuf kbs_b, kbl_b, kbs_a, kbl_a;
+    int64_t kb_nonzero[2] = {0, 0}, kb_total[2] = {0, 0};
     size_t smem = 0;
     int* err = nullptr;
     // exact diagonal H_II of the whole H (same-spin diagonals and the opposite-spin
