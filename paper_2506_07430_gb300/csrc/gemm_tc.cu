@@ -41,7 +41,15 @@
 namespace kpm {
 namespace {
 
-constexpr int GM_BM = 128, GM_BN = 256, GM_BK = 64, GM_STAGES = 2;
+// k-block 64 (128-byte rows, SWIZZLE_128B) two stages deep, or 32 (64-byte rows,
+// SWIZZLE_64B) four stages deep: the same 192 KB of shared memory.  (Measured at
+// 16 orbitals: 32 is slower, 22 vs 19.5 ms for both products; the epilogue then
+// drains an accumulator chunk every 800 cycles of MMA.)
+#ifndef GM_BK_N
+#define GM_BK_N 64
+#endif
+constexpr int GM_BM = 128, GM_BN = 256, GM_BK = GM_BK_N, GM_STAGES = GM_BK == 64 ? 2 : 4;
+static_assert(GM_BK == 32 || GM_BK == 64, "k-block of 32 or 64");
 constexpr int GM_EPI_WARPS = 8;               // 2 per TMEM lane quadrant, 128 columns each
 constexpr int GM_TMA_WARP = GM_EPI_WARPS;       // producer (one thread)
 constexpr int GM_MMA_WARP = GM_EPI_WARPS + 1;   // MMA issue (one thread)
@@ -58,8 +66,8 @@ constexpr int GM_CK = 1;                        // k-blocks per accumulation chu
 #ifndef GM_BACKOFF_NS
 #define GM_BACKOFF_NS 256
 #endif
-constexpr uint32_t A_BYTES = GM_BM * GM_BK * 2;  // 16 KB per piece
-constexpr uint32_t B_BYTES = GM_BN * GM_BK * 2;  // 32 KB per piece
+constexpr uint32_t A_BYTES = GM_BM * GM_BK * 2;  // per piece
+constexpr uint32_t B_BYTES = GM_BN * GM_BK * 2;  // per piece
 constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr long long GM_WAIT = 4000000000LL;
 
@@ -133,15 +141,17 @@ __device__ __forceinline__ void ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// K-major SWIZZLE_128B descriptor: 8-row x 128-byte atoms, SBO = 1024 bytes
-// between atoms along M/N; the leading offset is unused for this layout.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+// K-major swizzled descriptor: atoms of 8 rows x (2 GM_BK) bytes (one k-block
+// row each), SBO = 8 rows between atoms along M/N; the leading offset is unused
+// for these layouts.  Layout type 2: SWIZZLE_128B, 4: SWIZZLE_64B.
+__device__ __forceinline__ uint64_t sw_desc(uint32_t saddr) {
+    constexpr uint32_t row_bytes = GM_BK * 2;
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)1 << 16;                 // LBO (ignored)
-    d |= (uint64_t)(1024 >> 4) << 32;       // SBO
-    d |= (uint64_t)1 << 46;                 // version
-    d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
+    d |= (uint64_t)1 << 16;                           // LBO (ignored)
+    d |= (uint64_t)((8 * row_bytes) >> 4) << 32;      // SBO
+    d |= (uint64_t)1 << 46;                           // version
+    d |= (uint64_t)(GM_BK == 64 ? 2 : 4) << 61;       // swizzle mode
     return d;
 }
 
@@ -311,15 +321,15 @@ k_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensor
                     // sum is small, then the main products (hi x hi)
 #pragma unroll
                     for (int j = 0; j < GM_BK / 16; ++j) {
-                        const uint32_t off = j * 32;  // 16 FP16 = 32 bytes along K in the atom row
+                        const uint32_t off = j * 32;  // 16 FP16 = 32 bytes along K in the row
                         const uint32_t acc0 = (kb != c * ck || j != 0) ? 1u : 0u;
-                        mma_ss(d, sw128_desc(a1 + off), sw128_desc(b0 + off), idesc, acc0);
-                        mma_ss(d, sw128_desc(a0 + off), sw128_desc(b1 + off), idesc, 1);
+                        mma_ss(d, sw_desc(a1 + off), sw_desc(b0 + off), idesc, acc0);
+                        mma_ss(d, sw_desc(a0 + off), sw_desc(b1 + off), idesc, 1);
                     }
 #pragma unroll
                     for (int j = 0; j < GM_BK / 16; ++j) {
                         const uint32_t off = j * 32;
-                        mma_ss(d, sw128_desc(a0 + off), sw128_desc(b0 + off), idesc, 1);
+                        mma_ss(d, sw_desc(a0 + off), sw_desc(b0 + off), idesc, 1);
                     }
                     mma_commit_(&empty[s]);
                 }
@@ -522,7 +532,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // 2-D FP16 tensor map: rows x cols (cols innermost, row pitch in elements),
-// box = 64 columns x box_rows rows, 128-byte swizzle, zero fill out of bounds.
+// box = GM_BK columns x box_rows rows, swizzled rows of GM_BK elements (the
+// layout sw_desc describes), zero fill out of bounds.
 CUtensorMap make_map(const __half* base, int64_t rows, int64_t cols, int64_t pitch, int box_rows) {
     auto fn = encode_fn();
     if (!fn) KPM_THROW(KPM_ECUDA, "cuTensorMapEncodeTiled is not available");
@@ -531,10 +542,11 @@ CUtensorMap make_map(const __half* base, int64_t rows, int64_t cols, int64_t pit
     CUtensorMap m;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)(pitch * 2)};
-    cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+    cuuint32_t box[2] = {(cuuint32_t)GM_BK, (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
     CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (void*)base, dims, strides, box, es,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    GM_BK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) KPM_THROW(KPM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return m;
