@@ -6,8 +6,8 @@
 // F_s is the Slater-Condon matrix of one spin's strings (tables.cu), symmetric,
 // with about 6.6 % nonzeros at 16 orbitals spread over most tiles (83 % of the
 // 128 x 128 tiles hold a nonzero), so both products run as dense GEMMs that skip
-// only the all-zero k-blocks of the matrix operand's tile (22 % of the 128 x 64
-// blocks of F_b, 15 % of the 256 x 64 blocks of F_a at 16 orbitals):
+// only the all-zero k-blocks of the matrix operand's tile (15 % of the 256 x 64
+// blocks of F_b and of F_a at 16 orbitals; tiles are taken in pairs, below):
 // out[m][n] = sum_k A[m][k] B[n][k] with both operands K-major,
 //   beta:  A = F_b (m = I_b, k = J),      B = C (n = I_a, k = J)
 //   alpha: A = C^T (m = I_b, k = J),      B = F_a (n = I_a, k = J)
@@ -24,7 +24,8 @@
 // Kernel: CTA tile 128 x 256, k-block 64 (128 bytes per row: one SWIZZLE_128B
 // atom row), two-stage TMA pipeline (full/empty mbarriers), one warp issues TMA,
 // one issues MMAs, eight warps drain accumulator chunks (see k_gemm) and run the
-// epilogue.  All waits are bounded.
+// epilogue; clusters of two CTAs on vertically adjacent tiles share (multicast)
+// the B tile.  All waits are bounded.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
@@ -48,9 +49,19 @@ namespace {
 #ifndef GM_BK_N
 #define GM_BK_N 64
 #endif
-constexpr int GM_BM = 128, GM_BN = 256, GM_BK = GM_BK_N, GM_STAGES = GM_BK == 64 ? 2 : 4;
+// N of a tile: 256 (8 epilogue warps of 128 columns) or 192 (12 of 64 columns,
+// half the tensor-memory loads per warp and chunk; measured slower at 16 orbitals,
+// 20.4 vs 19.6 ms for both products)
+#ifndef GM_BN_N
+#define GM_BN_N 256
+#endif
+constexpr int GM_BM = 128, GM_BN = GM_BN_N, GM_BK = GM_BK_N, GM_STAGES = GM_BK == 64 ? 2 : 4;
 static_assert(GM_BK == 32 || GM_BK == 64, "k-block of 32 or 64");
-constexpr int GM_EPI_WARPS = 8;               // 2 per TMEM lane quadrant, 128 columns each
+// epilogue warps: GM_BN / GM_EPI_COLS per TMEM lane quadrant, GM_EPI_COLS columns
+// each, drained 32 columns per tensor-memory load
+constexpr int GM_EPI_COLS = GM_BN == 256 ? 128 : 64;
+constexpr int GM_EPI_WARPS = 4 * GM_BN / GM_EPI_COLS;
+static_assert(GM_BN % GM_EPI_COLS == 0 && GM_EPI_COLS % 32 == 0, "epilogue geometry");
 constexpr int GM_TMA_WARP = GM_EPI_WARPS;       // producer (one thread)
 constexpr int GM_MMA_WARP = GM_EPI_WARPS + 1;   // MMA issue (one thread)
 constexpr int GM_THREADS = 32 * (GM_EPI_WARPS + 2);
@@ -68,6 +79,10 @@ constexpr int GM_CK = 1;                        // k-blocks per accumulation chu
 #endif
 constexpr uint32_t A_BYTES = GM_BM * GM_BK * 2;  // per piece
 constexpr uint32_t B_BYTES = GM_BN * GM_BK * 2;  // per piece
+// CTA pairs (clusters of two) on vertically adjacent tiles share the B tile: each
+// CTA loads half of its rows and multicasts them into both
+constexpr int GM_PAIR = 2;
+constexpr uint32_t B_HALF = B_BYTES / GM_PAIR;
 constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr long long GM_WAIT = 4000000000LL;
 
@@ -107,6 +122,25 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(su32(bar))
         : "memory");
 }
+// the same load multicast into every CTA of `mask` (same shared-memory offset,
+// completing bytes on the mbarrier at the same offset in each)
+__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                               uint64_t* bar, uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%2, %3}], [%4], %5;"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(su32(bar)), "h"(mask)
+        : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// all threads of both CTAs of the cluster
+__device__ __forceinline__ void cluster_sync_() {
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
 __device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
@@ -126,6 +160,13 @@ __device__ __forceinline__ void mma_ss(uint32_t d, uint64_t a, uint64_t b, uint3
 __device__ __forceinline__ void mma_commit_(uint64_t* b) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                  ::"r"(su32(b)) : "memory");
+}
+// arrive (once MMAs complete) on the mbarrier at this offset in every CTA of mask
+__device__ __forceinline__ void mma_commit_mc(uint64_t* b, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;"
+        ::"r"(su32(b)), "h"(mask) : "memory");
 }
 __device__ __forceinline__ void ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
@@ -203,6 +244,14 @@ __device__ __forceinline__ void mbar_arrive_(uint64_t* b) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
 }
 
+// Cluster pairs: the two CTAs of a cluster compute row tiles 2 p and 2 p + 1 of
+// the same column tile and share its B operand: CTA r loads B rows
+// [n0 + 128 r, n0 + 128 r + 128) of each piece and multicasts them to both, so
+// each CTA reads 64 of the 96 KB of a stage from L2.  A stage is reloaded only
+// when the MMAs of both CTAs have released it (the MMA commits arrive on the
+// "empty" barrier of both CTAs), and both CTAs sync at the start (barriers
+// initialised) and at the end (no multicast or remote arrive left in flight).
+//
 // Accumulation in chunks: the MMA thread restarts the accumulator every ck
 // k-blocks, alternating two tensor-memory accumulators of GM_BN columns; the
 // epilogue warps add each finished chunk into FP32 running sums held in
@@ -210,7 +259,7 @@ __device__ __forceinline__ void mbar_arrive_(uint64_t* b) {
 // one rounding per k-step over all of K (12870 at 16 orbitals) carries an error
 // growing like sqrt(K); in chunks, each accumulator sums a short run and the
 // running sum takes one rounding per chunk.
-__global__ void __launch_bounds__(GM_THREADS, 1)
+__global__ void __cluster_dims__(GM_PAIR, 1, 1) __launch_bounds__(GM_THREADS, 1)
 k_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
        const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
        const GemmArgs g) {
@@ -227,22 +276,28 @@ k_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensor
     int* consumed = issued + 1;                       // stages the MMA thread passed
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // grouped rasterisation: groups of GROUP_M row tiles walk all column tiles,
-    // so the group's A panels and the current B panels stay in L2
+    const uint32_t crank = cluster_rank();
+    // grouped rasterisation over pairs of row tiles: groups of GROUP_M pairs walk
+    // all column tiles, so the group's A panels and the current B panels stay in L2
     const int GROUP_M = g.group_m;
     const int nM = (g.M + GM_BM - 1) / GM_BM, nN = (g.N + GM_BN - 1) / GM_BN;
-    const int b = blockIdx.x;
+    const int nMP = (nM + GM_PAIR - 1) / GM_PAIR;
+    const int b = blockIdx.x / GM_PAIR;
     const int gsize = GROUP_M * nN;
     const int first_m = (b / gsize) * GROUP_M;
-    const int gm = min(nM - first_m, GROUP_M);
-    const int m0 = (first_m + (b % gsize) % gm) * GM_BM;
+    const int gm = min(nMP - first_m, GROUP_M);
+    const int mp = first_m + (b % gsize) % gm;
+    // (with an odd number of row tiles the last pair's second tile lies past M:
+    // its A loads read the zero fill and its epilogue writes nothing)
+    const int m0 = (mp * GM_PAIR + (int)crank) * GM_BM;
     const int n0 = ((b % gsize) / gm) * GM_BN;
-    // k-blocks this tile visits: all of K, or the list of blocks where the matrix
-    // operand's tile has a nonzero
+    // k-blocks the pair visits (both CTAs the same, as they share the B loads): all
+    // of K, or the blocks where the matrix operand's tile (the pair's 256 rows of
+    // A, or the 256-row B tile) has a nonzero
     int nk = (g.K + GM_BK - 1) / GM_BK;
     const int* klist = nullptr;
     if (g.kbs) {
-        const int t = g.kb_by_n ? n0 / GM_BN : m0 / GM_BM;
+        const int t = g.kb_by_n ? n0 / GM_BN : mp;
         klist = g.kbl + g.kbs[t];
         nk = g.kbs[t + 1] - g.kbs[t];
     }
@@ -252,7 +307,7 @@ k_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensor
     if (tid == 0) {
         for (int s = 0; s < GM_STAGES; ++s) {
             mbar_init_(&full[s], 1);
-            mbar_init_(&empty[s], 1);
+            mbar_init_(&empty[s], GM_PAIR);   // the MMA commits of both CTAs
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init_(&accf[i], 1);
@@ -274,6 +329,7 @@ k_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensor
     }
     tc_before();
     __syncthreads();
+    cluster_sync_();   // the peer's barriers are initialised before any multicast or remote arrive
     tc_after();
     const uint32_t tmem = *holder;
 
@@ -290,8 +346,11 @@ k_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensor
                 const int kx = (klist ? klist[kb] : kb) * GM_BK;
                 tma_load_2d(su32(st), &mA0, kx, m0, &full[s]);
                 tma_load_2d(su32(st + A_BYTES), &mA1, kx, m0, &full[s]);
-                tma_load_2d(su32(st + 2 * A_BYTES), &mB0, kx, n0, &full[s]);
-                tma_load_2d(su32(st + 2 * A_BYTES + B_BYTES), &mB1, kx, n0, &full[s]);
+                // this CTA's half of the B rows, into both CTAs
+                const uint32_t hb = crank * B_HALF;
+                const int nh = n0 + (int)crank * (GM_BN / GM_PAIR);
+                tma_load_2d_mc(su32(st + 2 * A_BYTES + hb), &mB0, kx, nh, &full[s], 0x3);
+                tma_load_2d_mc(su32(st + 2 * A_BYTES + B_BYTES + hb), &mB1, kx, nh, &full[s], 0x3);
                 *(volatile int*)issued = kb + 1;
             }
         }
@@ -331,7 +390,7 @@ k_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensor
                         const uint32_t off = j * 32;
                         mma_ss(d, sw_desc(a0 + off), sw_desc(b0 + off), idesc, 1);
                     }
-                    mma_commit_(&empty[s]);
+                    mma_commit_mc(&empty[s], 0x3);   // stage s released in both CTAs
                 }
                 if (!ok) break;
                 mma_commit_(&accf[c & 1]);
@@ -340,10 +399,10 @@ k_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensor
     } else {
         // epilogue warps: running sums of columns [128 h, 128 h + 128) for row m
         const int quad = warp & 3, h = warp >> 2;
-        const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(h * 128);
-        float rs[128];
+        const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(h * GM_EPI_COLS);
+        float rs[GM_EPI_COLS];
 #pragma unroll
-        for (int u = 0; u < 128; ++u) rs[u] = 0.f;
+        for (int u = 0; u < GM_EPI_COLS; ++u) rs[u] = 0.f;
         bool ok = true;
         for (int c = 0; c < nchunk && ok; ++c) {
             if (lane == 0)
@@ -353,7 +412,7 @@ k_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensor
             tc_after();
             const uint32_t src = trow + (uint32_t)((c & 1) * GM_BN);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < GM_EPI_COLS / 32; ++q) {
                 uint32_t r[32];
                 ld32(src + (uint32_t)(q * 32), r);
 #pragma unroll
@@ -376,8 +435,8 @@ k_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensor
             const int m = m0 + quad * 32 + lane;
             if (m < g.M) {
 #pragma unroll
-                for (int u = 0; u < 128; ++u) {
-                    const int n = n0 + h * 128 + u;
+                for (int u = 0; u < GM_EPI_COLS; ++u) {
+                    const int n = n0 + h * GM_EPI_COLS + u;
                     if (n < g.N) {
                         const int64_t o = (int64_t)n * g.ldy + m;
                         float v = g.y[o] + rs[u] * scale;
@@ -401,6 +460,7 @@ k_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensor
             mbar_wait_bounded(&full[kb % GM_STAGES], (kb / GM_STAGES) & 1, g.err);
     }
     __syncthreads();
+    cluster_sync_();   // neither CTA exits while the peer may still write into it
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem)
                      : "memory");
@@ -556,6 +616,12 @@ CUtensorMap make_map(const __half* base, int64_t rows, int64_t cols, int64_t pit
 
 int64_t half_pitch(int64_t cols) { return (cols + 7) / 8 * 8; }
 
+// CTAs of an M x N product: pairs of row tiles x column tiles, two CTAs each
+static unsigned gemm_grid(int64_t M, int64_t N) {
+    const int64_t nM = (M + GM_BM - 1) / GM_BM, nN = (N + GM_BN - 1) / GM_BN;
+    return (unsigned)(GM_PAIR * ((nM + GM_PAIR - 1) / GM_PAIR) * nN);
+}
+
 static double offdiag_scale(const SpinTables& T, DevBuf& scratch, cudaStream_t st) {
     scratch.ensure(sizeof(unsigned long long));
     KPM_CUDA(cudaMemsetAsync(scratch.p, 0, sizeof(unsigned long long), st));
@@ -654,9 +720,9 @@ void DenseSS::init(const SpinTables& A, const SpinTables& B, bool same, int* err
         fa_lo = &fa_lo_own;
         da = &da_own;
     }
-    // beta: F_b is the A operand (GM_BM-row tiles); alpha: F_a is the B operand
-    // (GM_BN-row tiles)
-    block_lists(B, GM_BM, kbs_b, kbl_b, &kb_nonzero[0], &kb_total[0], st);
+    // beta: F_b is the A operand (pairs of GM_BM-row tiles); alpha: F_a is the B
+    // operand (GM_BN-row tiles)
+    block_lists(B, GM_PAIR * GM_BM, kbs_b, kbl_b, &kb_nonzero[0], &kb_total[0], st);
     block_lists(A, GM_BN, kbs_a, kbl_a, &kb_nonzero[1], &kb_total[1], st);
 }
 
@@ -672,11 +738,11 @@ void DenseSS::split(const float* x, const float* amax, cudaStream_t st) {
 void DenseSS::launch_beta(float* y, const float* amax, int group, cudaStream_t st) {
     CUtensorMap a0 = make_map(fb_hi.as<__half>(), nb, nb, pb, GM_BM);
     CUtensorMap a1 = make_map(fb_lo.as<__half>(), nb, nb, pb, GM_BM);
-    CUtensorMap b0 = make_map(xh.as<__half>(), na, nb, xpitch, GM_BN);
-    CUtensorMap b1 = make_map(xl.as<__half>(), na, nb, xpitch, GM_BN);
+    CUtensorMap b0 = make_map(xh.as<__half>(), na, nb, xpitch, GM_BN / GM_PAIR);
+    CUtensorMap b1 = make_map(xl.as<__half>(), na, nb, xpitch, GM_BN / GM_PAIR);
     GemmArgs g{(int)nb, (int)na, (int)nb, y, nb, 1.0f, amax, (float)wscale_b,
                nullptr, nullptr, err, group, kbs_b.as<int>(), kbl_b.as<int>(), 0};
-    dim3 grid((unsigned)(((nb + GM_BM - 1) / GM_BM) * ((na + GM_BN - 1) / GM_BN)));
+    dim3 grid(gemm_grid(nb, na));
     k_gemm<<<grid, GM_THREADS, smem, st>>>(a0, a1, b0, b1, g);
     KPM_LAUNCHED();
 }
@@ -687,11 +753,11 @@ void DenseSS::launch_alpha(const float* x, float* y, const float* amax, int grou
     const float* diag = diag_full ? x : nullptr;
     CUtensorMap a0 = make_map(th.as<__half>(), nb, na, pa, GM_BM);
     CUtensorMap a1 = make_map(tl.as<__half>(), nb, na, pa, GM_BM);
-    CUtensorMap b0 = make_map(fa_hi->as<__half>(), na, na, pa, GM_BN);
-    CUtensorMap b1 = make_map(fa_lo->as<__half>(), na, na, pa, GM_BN);
+    CUtensorMap b0 = make_map(fa_hi->as<__half>(), na, na, pa, GM_BN / GM_PAIR);
+    CUtensorMap b1 = make_map(fa_lo->as<__half>(), na, na, pa, GM_BN / GM_PAIR);
     GemmArgs g{(int)nb, (int)na, (int)na, y, nb, 1.0f, amax, (float)wscale_a,
                diag, diag ? diag_full : nullptr, err, group, kbs_a.as<int>(), kbl_a.as<int>(), 1};
-    dim3 grid((unsigned)(((nb + GM_BM - 1) / GM_BM) * ((na + GM_BN - 1) / GM_BN)));
+    dim3 grid(gemm_grid(nb, na));
     k_gemm<<<grid, GM_THREADS, smem, st>>>(a0, a1, b0, b1, g);
     KPM_LAUNCHED();
 }
