@@ -97,6 +97,11 @@ def parse_args():
                         "also run plain (FP64, one at a time)")
     p.add_argument("--plain-max-norb", type=int, default=12)
     p.add_argument("--serve-slots", type=int, default=8)
+    p.add_argument("--serve-rate-frac", type=float, default=0.8,
+                   help="--serving: also run the stream at a seeded Poisson arrival rate of this "
+                        "fraction of the measured all-at-once capacity (0: skip)")
+    p.add_argument("--no-serving-check", action="store_true",
+                   help="skip the compact served-vs-plain check of the default line")
     p.add_argument("--graphs-compare", type=int, default=0, metavar="NSTEPS",
                    help="time NSTEPS Chebyshev steps of --workload/--precision with the steps "
                         "replayed from CUDA graphs and issued kernel by kernel")
@@ -451,6 +456,8 @@ def run_ours(args, ws, rank, local, pg):
     if cpu is not None:
         out["cpu_baseline"] = cpu
     k.close()
+    if rank == 0 and ws == 1 and not args.no_serving_check:
+        out["serving_check"] = serving_check(args)
     return out
 
 
@@ -748,9 +755,70 @@ def _percentile(xs, q):
     return xs[f] + (xs[c] - xs[f]) * (k - f)
 
 
+def serve_items(args, items, precision, slots, arrivals=None):
+    """Serves (request, integrals, psi, a, b) items through one Server and returns
+    the results and a summary.  With `arrivals` (seconds from the start) each
+    request is submitted at its arrival time; latencies run from submission."""
+    from paper_2506_07430_gb300 import Server
+
+    srv = Server(mem_budget_bytes=int(args.serve_budget_gb * (1 << 30)), max_slots=slots,
+                 steps_per_round=16, precision=precision)
+    t0 = time.perf_counter()
+    ids = []
+    for i, (r, I, psi, a, b) in enumerate(items):
+        if arrivals is not None:
+            dt = t0 + arrivals[i] - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+        ids.append(srv.submit(I.h1, I.eri, I.dipole, r["norb"], r["nalpha"], r["nbeta"], psi,
+                              0b111, a, b, r["nmoments"], npoints=2048))
+    res = [srv.wait(i, timeout_ms=3600 * 1000, allow_ebounds=True) for i in ids]
+    t1 = time.perf_counter()
+    srv.close()
+    lat = [x["t_total_s"] for x in res]
+    return res, {"requests": len(items), "seconds": round(t1 - t0, 3),
+                 "spectra_per_s": round(len(items) / (t1 - t0), 4),
+                 "p50_latency_s": round(_percentile(lat, 0.5), 4),
+                 "p99_latency_s": round(_percentile(lat, 0.99), 4),
+                 "statuses": sorted(set(int(x["status"]) for x in res))}
+
+
+def serving_check(args, nreq=3, norb=10, nmoments=1024):
+    """Compact served-vs-plain key of the default line: nreq requests at
+    norb/norb electrons (x/y/z block, nmoments moments, seeded integrals and
+    states), served in KPM_MIXED by the continuous-batching server against plain
+    KPM_FP64 one at a time: spectra/s, latencies and the served results' errors."""
+    from paper_2506_07430_gb300 import KPM
+
+    ne = norb // 2
+    items = []
+    for r in range(nreq):
+        seed = 2506300 + r
+        I = synthetic.integrals(norb, ne, ne, seed)
+        k = KPM(I.h1, I.eri, I.dipole, norb, ne, ne, precision="mixed")
+        emin, emax = k.bounds(iters=args.lanczos, seed=seed)
+        a, b = KPM.scale(emin, emax)
+        psi = synthetic.random_state(k.dim, seed + 7)
+        k.close()
+        items.append((dict(norb=norb, nalpha=ne, nbeta=ne, nmoments=nmoments), I, psi, a, b))
+    plain, p_st = serve_items(args, items, "fp64", 1)
+    served, s_st = serve_items(args, items, "mixed", 8)
+    mom_err = max(float(np.max(np.abs(rs["moments"] - rp["moments"]) / np.abs(rp["moments"][:, :1])))
+                  for rs, rp in zip(served, plain))
+    spec_err = max(float(np.linalg.norm(rs["intensity"] - rp["intensity"])
+                         / np.linalg.norm(rp["intensity"])) for rs, rp in zip(served, plain))
+    return {"requests": f"{nreq} x {norb}o/{norb}e, x/y/z, {nmoments} moments, seeded states",
+            "served_mixed": s_st, "plain_fp64": p_st,
+            "speedup": round(s_st["spectra_per_s"] / p_st["spectra_per_s"], 3),
+            "max_moment_err_over_omega0": mom_err, "max_spectrum_rel_l2": spec_err,
+            "within_target": bool(mom_err <= 1e-6 and spec_err <= 1e-4)}
+
+
 def run_serving(args):
     """Serving workload: a stream of spectrum requests (sizes 10o/12o/14o, 512-2048
-    moments, x/y/z dipole components as one 3-column block), all submitted at t = 0.
+    moments, x/y/z dipole components as one 3-column block), all submitted at t = 0,
+    and again at a seeded Poisson rate (--serve-rate-frac of the capacity measured
+    at t = 0).
     Served: the continuous-batching server (several resident requests, interleaved
     rounds of Chebyshev steps) in KPM_MIXED over the whole stream, and in KPM_MIXED
     and KPM_FP32 over a subset; plain: KPM_FP64, one request at a time (max_slots =
@@ -776,25 +844,19 @@ def run_serving(args):
         prep.append((r, I, psi, a, b))
     torch.cuda.synchronize()
 
-    def serve(items, precision, slots):
-        srv = Server(mem_budget_bytes=int(args.serve_budget_gb * (1 << 30)), max_slots=slots,
-                     steps_per_round=16, precision=precision)
-        t0 = time.perf_counter()
-        ids = [srv.submit(I.h1, I.eri, I.dipole, r["norb"], r["nalpha"], r["nbeta"], psi, 0b111,
-                          a, b, r["nmoments"], npoints=2048)
-               for r, I, psi, a, b in items]
-        res = [srv.wait(i, timeout_ms=3600 * 1000, allow_ebounds=True) for i in ids]
-        t1 = time.perf_counter()
-        srv.close()
-        lat = [x["t_total_s"] for x in res]
-        return res, {"requests": len(items), "seconds": round(t1 - t0, 3),
-                     "spectra_per_s": round(len(items) / (t1 - t0), 4),
-                     "p50_latency_s": round(_percentile(lat, 0.5), 4),
-                     "p99_latency_s": round(_percentile(lat, 0.99), 4),
-                     "statuses": sorted(set(int(x["status"]) for x in res))}
+    def serve(items, precision, slots, arrivals=None):
+        return serve_items(args, items, precision, slots, arrivals)
 
     sub = [x for x in prep if x[0]["norb"] <= args.plain_max_norb][:args.plain_requests]
     served_all, s_all = serve(prep, "mixed", args.serve_slots)
+    # the same stream at a seeded Poisson rate, a fraction of the capacity just measured
+    s_poisson = None
+    if args.serve_rate_frac > 0:
+        rate = args.serve_rate_frac * s_all["spectra_per_s"]
+        arr = [r["arrival_s"] for r in synthetic.serving_stream(args.serve_requests, rate_hz=rate)]
+        _, s_poisson = serve(prep, "mixed", args.serve_slots, arrivals=arr)
+        s_poisson["rate_hz"] = round(rate, 4)
+        s_poisson["rate_fraction_of_capacity"] = args.serve_rate_frac
     plain_sub, p_sub = serve(sub, "fp64", 1)
     subset = {}
     for prec in ("mixed", "fp32"):
@@ -842,6 +904,7 @@ def run_serving(args):
                    "sizes": sizes, "slots": args.serve_slots,
                    "budget_gb": args.serve_budget_gb, "steps_per_round": 16},
         "served_stream_mixed": s_all,
+        "served_stream_mixed_poisson": s_poisson,
         "plain_subset_fp64": p_sub,
         "served_subset": subset,
         "subset": f"first {len(sub)} requests of the stream with <= {args.plain_max_norb} orbitals",
