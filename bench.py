@@ -894,10 +894,15 @@ def run_serving(args):
     for r in reqs:
         key = f"{r['norb']}o"
         sizes[key] = sizes.get(key, 0) + 1
+    # the value: the fastest served precision whose results meet the accuracy target
+    ok = [p for p in ("mixed", "fp32") if subset[p]["max_moment_err_over_omega0"] <= 1e-6
+          and subset[p]["max_spectrum_rel_l2"] <= 1e-4]
+    best = max(ok, key=lambda p: subset[p]["spectra_per_s"]) if ok else None
     return {
         "metric": "spectra/s, served (continuous batching) vs plain (FP64, one at a time); value: "
-                  "served FP32 (within the accuracy target) on the subset",
-        "value": subset["fp32"]["spectra_per_s"], "unit": "spectra/s", "n_gpus": 1,
+                  "the fastest served precision within the accuracy target, on the subset",
+        "value": subset[best]["spectra_per_s"] if best else None, "value_precision": best,
+        "unit": "spectra/s", "n_gpus": 1,
         "higher_is_better": True, "vs_baseline": None, "data": "synthetic",
         "config": {"workload": "serving stream (10o/12o/14o, 512-2048 moments, x/y/z block, "
                                "all arrivals at t=0)",
