@@ -370,6 +370,23 @@ kpm_status kpm_synchronize(kpm_ctx* ctx);
 kpm_status kpm_tuned_params(const kpm_ctx* ctx, int* group_beta, int* group_alpha);
 
 /*
+ * kpm_tuned_rowpass -- the autotuner's choices for the opposite-spin row pass
+ * of a tensor-core context: the number of shared-memory stages of its gathered
+ * A tiles (2 or 3; 3 only where shared memory allows) and how many tiles ahead
+ * its copy warps prefetch the gathered rows into L2 (0, 4 or 8), picked by
+ * timing each pair once per device and shape at creation (shapes below 2^22
+ * determinants keep 3 or 2 stages and 4).  FP64 / FP32 contexts report 0, 0.
+ * Errors: KPM_EINVAL for NULL ctx.
+ *
+ * kpm_set_rowpass -- pins those two choices (results do not depend on them: the
+ * same products are formed in the same order, only the copies' timing moves).
+ * Errors: KPM_EINVAL for NULL ctx, a non-tensor-core context, stages outside
+ * 2..3 or beyond the shared memory sized at creation, prefetch outside 0..64.
+ */
+kpm_status kpm_tuned_rowpass(const kpm_ctx* ctx, int* stages, int* prefetch);
+kpm_status kpm_set_rowpass(kpm_ctx* ctx, int stages, int prefetch);
+
+/*
  * kpm_graphs_enable -- kpm_recursion_advance (and kpm_moments, the server)
  * issue pairs of Chebyshev steps as replays of CUDA graphs captured on first
  * use (one per assignment of the two rotating recursion vectors; the step

@@ -52,6 +52,8 @@ SIGNATURES = {
     "kpm_profile_read_rowpass": (_I, [_P, _P, _P]),
     "kpm_graphs_enable": (_I, [_P, _I]),
     "kpm_tuned_params": (_I, [_P, _P, _P]),
+    "kpm_tuned_rowpass": (_I, [_P, _P, _P]),
+    "kpm_set_rowpass": (_I, [_P, _I, _I]),
     "kpm_test_rowpass_stall": (_I, [_P, _I]),
     "kpm_spectrum_static": (_I, [_P, _I, _D, _D, _I, _I, _P, _P, _P]),
     "kpm_server_create": (_I, [_P, _P]),
@@ -321,6 +323,16 @@ class KPM:
         gb, ga = ctypes.c_int(), ctypes.c_int()
         _check(self._lib().kpm_tuned_params(self._h, ctypes.byref(gb), ctypes.byref(ga)), self._h)
         return gb.value, ga.value
+
+    def tuned_rowpass(self):
+        """Autotuner choices of the row pass: (A stages, L2 prefetch distance in tiles)."""
+        st, pf = ctypes.c_int(), ctypes.c_int()
+        _check(self._lib().kpm_tuned_rowpass(self._h, ctypes.byref(st), ctypes.byref(pf)), self._h)
+        return st.value, pf.value
+
+    def set_rowpass(self, stages: int, prefetch: int):
+        """Pins the row pass's A stages and prefetch distance (kpm_set_rowpass)."""
+        _check(self._lib().kpm_set_rowpass(self._h, int(stages), int(prefetch)), self._h)
 
     def test_rowpass_stall(self, on: bool = True):
         """Testing aid: the next tensor-core row pass stalls until its bounded waits

@@ -1149,6 +1149,30 @@ kpm_status kpm_tuned_params(const kpm_ctx* ctx, int* group_beta, int* group_alph
     return KPM_OK;
 }
 
+kpm_status kpm_tuned_rowpass(const kpm_ctx* ctx, int* stages, int* prefetch) {
+    if (!ctx) { g_err = "NULL context"; return KPM_EINVAL; }
+    if (stages) *stages = ctx->tc ? ctx->tc->nst : 0;
+    if (prefetch) *prefetch = ctx->tc ? ctx->tc->rp_prefetch : 0;
+    return KPM_OK;
+}
+
+kpm_status kpm_set_rowpass(kpm_ctx* ctx, int stages, int prefetch) {
+    if (!ctx) { g_err = "NULL context"; return KPM_EINVAL; }
+    if (!ctx->tc) {
+        ctx->err = "not a tensor-core (KPM_MIXED / KPM_MIXED_BF16) context";
+        return KPM_EINVAL;
+    }
+    const size_t need = kpm::rowpass_smem_bytes(*ctx->tc, stages);
+    if (stages < 2 || stages > 3 || prefetch < 0 || prefetch > 64 || need > ctx->tc->smem_bytes) {
+        ctx->err = "row pass: stages must be 2 or 3 (within the shared memory sized at "
+                   "creation) and prefetch 0..64 tiles";
+        return KPM_EINVAL;
+    }
+    ctx->tc->nst = stages;
+    ctx->tc->rp_prefetch = prefetch;
+    return KPM_OK;
+}
+
 kpm_status kpm_graphs_enable(kpm_ctx* ctx, int enable) {
     if (!ctx) { g_err = "NULL context"; return KPM_EINVAL; }
     ctx->graphs = enable != 0;

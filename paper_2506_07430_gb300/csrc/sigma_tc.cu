@@ -32,7 +32,10 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <array>
 #include <cmath>
+#include <map>
+#include <mutex>
 
 namespace kpm {
 
@@ -166,6 +169,7 @@ struct RowPass {
     int nexc_c;              // table entries per column string (contributions per target)
     int NS;                  // slots in use (n(n+1)/2); slots [NS, P) are padding
     int nst;                 // A stages in shared memory (2 or 3)
+    int prefetch;            // L2 prefetch of the A rows this many tiles ahead (0: none)
     int* err;
     long long wait_cycles;   // limit of every mbarrier wait (clock64 cycles)
     int stall;               // test of the bounded waits: the MMA thread issues nothing, so
@@ -194,11 +198,6 @@ constexpr int RP_SINK = 32;
 #endif
 #ifndef RP_SCATTER_BACKOFF_NS
 #define RP_SCATTER_BACKOFF_NS 64
-#endif
-// the copy warps prefetch the A rows of tile t + RP_PREFETCH into L2 when they
-// copy tile t (a quarter of the gathered segments miss L2; 0: no prefetch)
-#ifndef RP_PREFETCH
-#define RP_PREFETCH 4
 #endif
 constexpr uint32_t A_LBO = 2048;             // A stage: K-group (8 entries) stride, bytes
 constexpr uint32_t A_SBO = 128;              // A stage: MN-group (8 columns) stride, bytes
@@ -312,7 +311,7 @@ __device__ __forceinline__ bool wait_phase(uint64_t* mbar, uint32_t parity, vola
 //     stage t % nst once MMA(t - nst) has released it; once they have landed
 //     (and been fenced for the async proxy), each arrives on "A full"; with
 //     them, one lane per entry prefetches that entry's rows of tile
-//     t + RP_PREFETCH into L2;
+//     t + p.prefetch into L2 (a quarter of the gathered segments miss L2);
 //   MMA (warp 19, one thread): MMA(t) once A(t) is full and the scatter warps
 //     have released D buffer t & 1; tcgen05.commit then signals "stage free"
 //     and "D full";
@@ -568,12 +567,12 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
                     if (!ok) break;
                 }
                 copies(t, gt % nst);
-                if (RP_PREFETCH > 0 && t + RP_PREFETCH < ntiles) {
+                if (p.prefetch > 0 && t + p.prefetch < ntiles) {
                     // entry cw * 32 + lane: both pieces of its 128 columns (256 bytes each)
                     const int e = cw * 32 + lane;
                     const int64_t ro = e < KR ? rowoff[e] : -1;
                     if (ro >= 0) {
-                        const int64_t off = ro + (int64_t)(t + RP_PREFETCH) * 128;
+                        const int64_t off = ro + (int64_t)(t + p.prefetch) * 128;
                         prefetch_l2(p.Xh + off, 256u);
                         prefetch_l2(p.Xl + off, 256u);
                     }
@@ -901,6 +900,10 @@ void* rowpass_kernel(int P, bool fp16) {
 
 }  // namespace
 
+size_t rowpass_smem_bytes(const TcSigma& t, int stages) {
+    return rowpass_smem(t.P, t.nw, t.KR, t.nsa > t.nsb ? t.nsa : t.nsb, stages);
+}
+
 void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
                    const double* d_eri, const float2* d_diag, int norb, double wmax,
                    double wcolsum, bool use_fp16, cudaStream_t st) {
@@ -1001,10 +1004,10 @@ void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
     dense.init(A, B, &A == &B, err.as<int>(), st);
     dense.diag_full = d_diag;
     dense.autotune(st);
+    autotune(st);
 }
 
 void TcSigma::apply(const float* x, float* y, int ncol, cudaStream_t st) {
-    const uint32_t nc = tmem_cols(P);
     const int64_t xp = dense.xpitch;
     for (int c = 0; c < ncol; ++c) {
         const float* X = x + (size_t)c * dim;
@@ -1033,34 +1036,114 @@ void TcSigma::apply(const float* x, float* y, int ncol, cudaStream_t st) {
             xl = xbl.as<uint16_t>();
         }
         // opposite-spin part: rows alpha, columns beta; writes Y
-        RowPass p1{xh, xl, xp, Y, nsa, nsb, slot_b.as<uint4>(),
-                   rtgt_a.as<int32_t>(), rslot_a.as<uint16_t>(), noff, ndiag, KR,
-                   ta->masks.as<uint32_t>(), wdiag.as<double>(),
-                   wimg.as<uint16_t>(), nc, am, rowmax.as<float>(), wscale, tb->nexc, NS, nst,
-                   err.as<int>(), stall_next ? STALL_WAIT_CYCLES : WAIT_CYCLES,
-                   stall_next ? 1 : 0};
-        stall_next = false;
-        int g1 = (int)(nsa < nsm ? nsa : nsm);
-        void* args1[] = {&p1};
-        if (prof) {
-            if ((int)ev.size() < ev_used + 2) {
-                cudaEvent_t e0, e1;
-                KPM_CUDA(cudaEventCreate(&e0));
-                KPM_CUDA(cudaEventCreate(&e1));
-                ev.push_back(e0);
-                ev.push_back(e1);
-            }
-            KPM_CUDA(cudaEventRecord(ev[ev_used], st));
-        }
-        KPM_CUDA(cudaLaunchKernel(kernel, dim3(g1), dim3(RP_THREADS), args1, smem_bytes, st));
-        KPM_LAUNCHED();
-        if (prof) {
-            KPM_CUDA(cudaEventRecord(ev[ev_used + 1], st));
-            ev_used += 2;
-        }
+        launch_rowpass(xh, xl, Y, nst, rp_prefetch, st);
         // same-spin parts (dense GEMMs) and the exact diagonal, added into Y
         dense.apply(X, Y, am, st);
     }
+}
+
+void TcSigma::launch_rowpass(const uint16_t* xh, const uint16_t* xl, float* Y, int stages,
+                             int prefetch, cudaStream_t st) {
+    const uint32_t nc = tmem_cols(P);
+    const int64_t xp = dense.xpitch;
+    const float* am = reinterpret_cast<const float*>(amax.p);
+    RowPass p1{xh, xl, xp, Y, nsa, nsb, slot_b.as<uint4>(),
+               rtgt_a.as<int32_t>(), rslot_a.as<uint16_t>(), noff, ndiag, KR,
+               ta->masks.as<uint32_t>(), wdiag.as<double>(),
+               wimg.as<uint16_t>(), nc, am, rowmax.as<float>(), wscale, tb->nexc, NS, stages,
+               prefetch, err.as<int>(), stall_next ? STALL_WAIT_CYCLES : WAIT_CYCLES,
+               stall_next ? 1 : 0};
+    stall_next = false;
+    int g1 = (int)(nsa < nsm ? nsa : nsm);
+    void* args1[] = {&p1};
+    if (prof) {
+        if ((int)ev.size() < ev_used + 2) {
+            cudaEvent_t e0, e1;
+            KPM_CUDA(cudaEventCreate(&e0));
+            KPM_CUDA(cudaEventCreate(&e1));
+            ev.push_back(e0);
+            ev.push_back(e1);
+        }
+        KPM_CUDA(cudaEventRecord(ev[ev_used], st));
+    }
+    // (smem_bytes is sized for the most stages init allowed)
+    KPM_CUDA(cudaLaunchKernel(kernel, dim3(g1), dim3(RP_THREADS), args1, smem_bytes, st));
+    KPM_LAUNCHED();
+    if (prof) {
+        KPM_CUDA(cudaEventRecord(ev[ev_used + 1], st));
+        ev_used += 2;
+    }
+}
+
+// Picks the row pass's A stages and L2 prefetch distance by timing every
+// candidate once per device and shape (process-wide cache), on a zero vector:
+// the choice decides only when copies are issued, never what is computed, so
+// results do not depend on it.  Small shapes keep the defaults.
+void TcSigma::autotune(cudaStream_t st) {
+    if (nsa * nsb < ((int64_t)1 << 22)) return;
+    int dev = 0;
+    KPM_CUDA(cudaGetDevice(&dev));
+    static std::mutex mu;
+    static std::map<std::array<int64_t, 5>, std::array<int, 2>> cache;
+    const std::array<int64_t, 5> key{dev, n, nsa, nsb, fp16 ? 1 : 0};
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            nst = it->second[0];
+            rp_prefetch = it->second[1];
+            return;
+        }
+    }
+    const int64_t xp = dense.xpitch;
+    // two distinct operand buffers, as in use (x's hi and lo pieces are separate
+    // arrays, so the gathers touch twice the bytes of one)
+    DevBuf zh, zl, y;
+    zh.alloc((size_t)nsa * xp * 2);
+    zl.alloc((size_t)nsa * xp * 2);
+    y.alloc((size_t)dim * sizeof(float));
+    KPM_CUDA(cudaMemsetAsync(zh.p, 0, zh.bytes, st));
+    KPM_CUDA(cudaMemsetAsync(zl.p, 0, zl.bytes, st));
+    KPM_CUDA(cudaMemsetAsync(amax.p, 0, sizeof(unsigned), st));
+    rowmax.ensure((size_t)(nsa > 0 ? nsa : 1) * sizeof(float));
+    KPM_CUDA(cudaMemsetAsync(rowmax.p, 0, rowmax.bytes, st));
+    cudaEvent_t e0, e1;
+    KPM_CUDA(cudaEventCreate(&e0));
+    KPM_CUDA(cudaEventCreate(&e1));
+    const bool prof_was = prof;
+    prof = false;
+    const int maxst = nst;   // what shared memory allows (init)
+    const int pfs[3] = {0, 4, 8};
+    float best = 0.f;
+    int bst = nst, bpf = rp_prefetch;
+    launch_rowpass(zh.as<uint16_t>(), zl.as<uint16_t>(), y.as<float>(), nst, rp_prefetch, st);
+    for (int stg = 2; stg <= maxst; ++stg) {
+        for (int pf : pfs) {
+            // the faster of two launches
+            float ms = 0.f;
+            for (int rep = 0; rep < 2; ++rep) {
+                KPM_CUDA(cudaEventRecord(e0, st));
+                launch_rowpass(zh.as<uint16_t>(), zl.as<uint16_t>(), y.as<float>(), stg, pf, st);
+                KPM_CUDA(cudaEventRecord(e1, st));
+                KPM_CUDA(cudaEventSynchronize(e1));
+                float t = 0.f;
+                KPM_CUDA(cudaEventElapsedTime(&t, e0, e1));
+                if (rep == 0 || t < ms) ms = t;
+            }
+            if (best == 0.f || ms < best) {
+                best = ms;
+                bst = stg;
+                bpf = pf;
+            }
+        }
+    }
+    prof = prof_was;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    nst = bst;
+    rp_prefetch = bpf;
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = {nst, rp_prefetch};
 }
 
 double TcSigma::read_prof(cudaStream_t st, int* count) {

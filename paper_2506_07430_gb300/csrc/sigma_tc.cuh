@@ -32,7 +32,9 @@ struct TcSigma {
     DevBuf err;                   // int error flag (1: a bounded wait ran out)
     DevBuf amax;                  // max |x| (float bits): operand scale, fixed-point range
     DevBuf rowmax;                // [N_a] max |x| per row: per-row fixed-point range of the row pass
-    int nst = 2;                  // A stages of the row pass (3 where shared memory allows)
+    int nst = 2;                  // A stages of the row pass (at most 3, where shared memory
+                                  // allows; autotuned)
+    int rp_prefetch = 4;          // L2 prefetch distance of the row pass, tiles (autotuned)
     bool stall_next = false;      // test of the bounded waits: the next row pass stalls (see
                                   // kpm_test_rowpass_stall)
     size_t smem_bytes = 0;
@@ -44,6 +46,12 @@ struct TcSigma {
               const double* d_eri, const float2* d_diag, int n, double wmax, double wcolsum,
               bool use_fp16, cudaStream_t st);
     void apply(const float* x, float* y, int ncol, cudaStream_t st);
+    // One row-pass launch (opposite-spin part of y, overwriting it) from the split
+    // rows xh, xl, with the given A stages and prefetch distance.
+    void launch_rowpass(const uint16_t* xh, const uint16_t* xl, float* y, int stages,
+                        int prefetch, cudaStream_t st);
+    // Times the row pass's stages x prefetch candidates once per device and shape.
+    void autotune(cudaStream_t st);
     // Reads and clears the device error flag (synchronises the stream).
     int check(cudaStream_t st);
 
@@ -56,5 +64,8 @@ struct TcSigma {
     double read_prof(cudaStream_t st, int* count);
     ~TcSigma();
 };
+
+// Dynamic shared memory of one row-pass CTA with the given number of A stages.
+size_t rowpass_smem_bytes(const TcSigma& t, int stages);
 
 }  // namespace kpm

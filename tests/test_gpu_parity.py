@@ -739,6 +739,37 @@ def test_autotuned_gemm_groups(torch):
     k.close()
 
 
+def test_autotuned_rowpass_choices_leave_results_unchanged(torch):
+    """The row pass's autotuned A stages and L2 prefetch distance are among the
+    candidates (small shapes keep the defaults), and every choice gives the same
+    sigma bit for bit: only the timing of the copies moves."""
+    from paper_2506_07430_gb300 import KPMError
+    I = synthetic.integrals(8, 4, 4, 2506071)
+    k = _kpm(I, 8, 4, 4, "fp64")
+    assert k.tuned_rowpass() == (0, 0)
+    k.close()
+    I = synthetic.integrals(14, 7, 7, 2506074)
+    k = _kpm(I, 14, 7, 7, "mixed")
+    st, pf = k.tuned_rowpass()
+    assert st in (2, 3) and pf in (0, 4, 8)
+    x = torch.from_numpy(synthetic.random_state(k.dim, 11)).float().cuda()
+    y = torch.empty_like(x)
+    outs = []
+    for stages in (2, 3):
+        for prefetch in (0, 4, 8):
+            k.set_rowpass(stages, prefetch)
+            k.sigma(x, y)
+            k.synchronize()
+            outs.append(y.clone())
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
+    with pytest.raises(KPMError):
+        k.set_rowpass(4, 4)
+    with pytest.raises(KPMError):
+        k.set_rowpass(3, -1)
+    k.close()
+
+
 def test_rowpass_bounded_wait_expiry_reports_etimeout(torch):
     """A wait that nothing completes (testing aid: the row pass issues no MMAs)
     runs out after its short limit; the kernel returns early, kpm_synchronize
