@@ -42,7 +42,15 @@ UNIT = "steps/s"
 # SHA-256 (first 16 hex digits) of the kernel's source file at the time of the
 # capture: the bench reports the figure only while that source is unchanged,
 # else null (the counters describe another kernel).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    ("fci16o16e", "mixed"): {
+        "bytes": 12.40e9 + 0.661e9,
+        "source": "paper_2506_07430_gb300/csrc/sigma_tc.cu",
+        "source_sha16": "d30d58bbf32258bc",
+        "captured": "2026-12-04, GB300, one launch of k_rowpass<144> (1 pass)",
+        "profile": "profiles/k_rowpass_fci16o16e.md",
+    },
+}
 
 
 def _source_sha16(rel):
