@@ -6,7 +6,7 @@
 // F_s is the Slater-Condon matrix of one spin's strings (tables.cu), symmetric,
 // with about 6.6 % nonzeros at 16 orbitals spread over most tiles (83 % of the
 // 128 x 128 tiles hold a nonzero), so both products run as dense GEMMs that skip
-// only the all-zero k-blocks of the matrix operand's tile (15 % of the 256 x 64
+// only the all-zero k-blocks of the matrix operand's tile (17 % of the 256 x 32
 // blocks of F_b and of F_a at 16 orbitals; tiles are taken in pairs, below):
 // out[m][n] = sum_k A[m][k] B[n][k] with both operands K-major,
 //   beta:  A = F_b (m = I_b, k = J),      B = C (n = I_a, k = J)
@@ -21,8 +21,8 @@
 // diagonals and the opposite-spin Coulomb sums, evaluated in FP64 and stored as
 // float hi + lo per determinant) times x, hi and lo multiplied separately.
 //
-// Kernel: CTA tile 128 x 256, k-block 64 (128 bytes per row: one SWIZZLE_128B
-// atom row), two-stage TMA pipeline (full/empty mbarriers), one warp issues TMA,
+// Kernel: CTA tile 128 x 256, k-block 32 (64 bytes per row: one SWIZZLE_64B atom
+// row), four-stage TMA pipeline (full/empty mbarriers), one warp issues TMA,
 // one issues MMAs, eight warps drain accumulator chunks (see k_gemm) and run the
 // epilogue; clusters of two CTAs on vertically adjacent tiles share (multicast)
 // the B tile.  All waits are bounded.
@@ -42,12 +42,15 @@
 namespace kpm {
 namespace {
 
-// k-block 64 (128-byte rows, SWIZZLE_128B) two stages deep, or 32 (64-byte rows,
-// SWIZZLE_64B) four stages deep: the same 192 KB of shared memory.  (Measured at
-// 16 orbitals: 32 is slower, 22 vs 19.5 ms for both products; the epilogue then
-// drains an accumulator chunk every 800 cycles of MMA.)
+// k-block 32 (64-byte rows, SWIZZLE_64B) four stages deep, or 64 (128-byte rows,
+// SWIZZLE_128B) two stages deep: the same 192 KB of shared memory.  Four stages
+// keep three k-blocks of loads in flight (about 2300 cycles of MMA to hide the
+// L2 latency, against 1500 with two stages of 64).  Measured at 16 orbitals,
+// both products: 18.0 ms (32, accumulation chunks of two k-blocks), 19.8 ms
+// (64), 22.0 ms (32 with one-k-block chunks: the epilogue then drains a chunk
+// every 800 cycles of MMA).
 #ifndef GM_BK_N
-#define GM_BK_N 64
+#define GM_BK_N 32
 #endif
 // N of a tile: 256 (8 epilogue warps of 128 columns) or 192 (12 of 64 columns,
 // half the tensor-memory loads per warp and chunk; measured slower at 16 orbitals,
@@ -69,10 +72,11 @@ constexpr int GM_THREADS = 32 * (GM_EPI_WARPS + 2);
 // addition into the accumulator toward zero (it shrinks every running sum by up
 // to one unit in the last place), a bias that grows with the number of MMAs
 // accumulated and would act as a fixed scaling of H; restarting the accumulator
-// every k-block (12 MMAs, the 8 small correction products first, so that their
-// additions truncate at their own small scale) and adding the chunks into FP32
-// running sums in registers (round to nearest) keeps it near 4 units of 2^-24.
-constexpr int GM_CK = 1;                        // k-blocks per accumulation chunk
+// every 64 of K (12 MMAs; in each k-block the small correction products first,
+// so that most of their additions truncate at their own small scale) and adding
+// the chunks into FP32 running sums in registers (round to nearest) keeps it to
+// a few units of 2^-24.
+constexpr int GM_CK = 64 / GM_BK;               // k-blocks per accumulation chunk
 // poll interval of the epilogue warps' waits (a chunk accumulates for microseconds)
 #ifndef GM_BACKOFF_NS
 #define GM_BACKOFF_NS 256
