@@ -461,7 +461,8 @@ def run_ours(args, ws, rank, local, pg):
                         f"memory and the moments read back inside the timed region; bytes are "
                         f"per request"},
         "gpu_launches": int(launches),
-        "tuned": dict(zip(("gemm_group_beta", "gemm_group_alpha"), k.tuned_params())),
+        "tuned": {**dict(zip(("gemm_group_beta", "gemm_group_alpha"), k.tuned_params())),
+                  **dict(zip(("rowpass_stages", "rowpass_prefetch_tiles"), k.tuned_rowpass()))},
         "clocks": clk,
         "moments_ok": moments_ok,
         "accuracy": acc,

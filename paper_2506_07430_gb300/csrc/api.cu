@@ -1,5 +1,5 @@
 // extern "C" entry points of include/kpm.h: context set-up, sigma/dipole
-// dispatch, the KPM recursion driver, Lanczos bounds and the spectrum.
+// dispatch, the KPM recursion loop, Lanczos bounds and the spectrum.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
