@@ -283,6 +283,28 @@ def test_bounds_contain_spectrum(torch, sys8):
         k.close()
 
 
+def test_bounds_contain_spectrum_12o(torch):
+    """Beyond 8 orbitals the spectrum is not available in closed form, so the
+    bounds (24 Lanczos steps, as the benchmark uses them) are checked against
+    what is: the lower bound lies below the FP64 ground-state energy (converged
+    to a residual < 1e-8), and 1024 moments of a random state on the interval
+    they define stay within |mu_n| <= mu_0 (T_n grows like cosh(n acosh|x|) for
+    any part of the spectrum outside [-1, 1], which KPM_EBOUNDS would report)."""
+    I = synthetic.integrals(12, 6, 6, 2506072)
+    k = _kpm(I, 12, 6, 6, "fp64")
+    e0, res, _ = k.ground_state(iters=60, max_cycles=30, tol=1e-10)
+    assert res < 1e-8
+    lo, hi = k.bounds(iters=24, seed=2506001)
+    assert lo <= e0 + 1e-9, (lo, e0)
+    k.close()
+    k = _kpm(I, 12, 6, 6, "mixed")
+    a, b = k.scale(lo, hi)
+    psi = synthetic.random_state(k.dim, 5)
+    mom = k.moments(psi, 0b100, a, b, 1024)[0]
+    assert np.all(np.abs(mom) <= np.abs(mom[0]) * (1 + 1e-9))
+    k.close()
+
+
 def test_ebounds_detected(torch, sys8):
     from paper_2506_07430_gb300 import KPMError
     I, sc, E, U, a, b = sys8
