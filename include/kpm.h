@@ -74,7 +74,7 @@ typedef enum {
                           x and the integrals each split into 2 FP16 pieces with
                           power-of-two scales, 3 MMAs per product (hi*hi, lo*hi,
                           hi*lo), FP32 accumulation; same-spin diagonals added
-                          exactly; FP64 dots/moments; up to 16 orbitals               */
+                          exactly; FP64 dots/moments; up to 18 orbitals               */
     KPM_MIXED_BF16 = 3 /* as KPM_MIXED with split-BF16 operands (2 pieces each,
                           3 MMAs): ~16 significant bits per product                  */
 } kpm_precision;
@@ -385,6 +385,27 @@ kpm_status kpm_tuned_params(const kpm_ctx* ctx, int* group_beta, int* group_alph
  */
 kpm_status kpm_tuned_rowpass(const kpm_ctx* ctx, int* stages, int* prefetch);
 kpm_status kpm_set_rowpass(kpm_ctx* ctx, int stages, int prefetch);
+
+/*
+ * kpm_rowpass_layout -- how the opposite-spin row pass of a tensor-core context
+ * holds its targets: the plain layout (wide = 0, passes = 1: 15-bit target strings
+ * with the excitation sign in the slot table, one output row's sigma in shared
+ * memory) or the wide one (wide = 1: 16-bit targets, the sign taken from the
+ * column string's occupations, the targets split into `passes` ranges, one pass
+ * over the row's tiles per range).  Creation picks the plain layout where it fits
+ * and the wide one with the fewest passes otherwise (more than 32736 strings per
+ * spin, or a row's sigma beyond shared memory: 17 and 18 orbitals).  FP64 / FP32
+ * contexts report 0, 0.  Errors: KPM_EINVAL for NULL ctx.
+ *
+ * kpm_set_rowpass_passes -- passes >= 1 switches to the wide layout with that
+ * many passes, 0 back to the automatic choice.  The row sums are integer and
+ * order-independent, so every layout gives the same sigma bit for bit.  The wide
+ * kernel is compiled for 12, 17 and 18 orbitals only.  Errors: KPM_EINVAL for
+ * NULL ctx, a non-tensor-core context, passes outside 0..64, or no wide kernel for
+ * this size; KPM_EUNSUPPORTED if a pass's targets do not fit in shared memory.
+ */
+kpm_status kpm_rowpass_layout(const kpm_ctx* ctx, int* wide, int* passes);
+kpm_status kpm_set_rowpass_passes(kpm_ctx* ctx, int passes);
 
 /*
  * kpm_graphs_enable -- kpm_recursion_advance (and kpm_moments, the server)

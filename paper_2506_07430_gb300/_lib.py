@@ -54,6 +54,8 @@ SIGNATURES = {
     "kpm_tuned_params": (_I, [_P, _P, _P]),
     "kpm_tuned_rowpass": (_I, [_P, _P, _P]),
     "kpm_set_rowpass": (_I, [_P, _I, _I]),
+    "kpm_rowpass_layout": (_I, [_P, _P, _P]),
+    "kpm_set_rowpass_passes": (_I, [_P, _I]),
     "kpm_test_rowpass_stall": (_I, [_P, _I]),
     "kpm_spectrum_static": (_I, [_P, _I, _D, _D, _I, _I, _P, _P, _P]),
     "kpm_server_create": (_I, [_P, _P]),
@@ -333,6 +335,16 @@ class KPM:
     def set_rowpass(self, stages: int, prefetch: int):
         """Pins the row pass's A stages and prefetch distance (kpm_set_rowpass)."""
         _check(self._lib().kpm_set_rowpass(self._h, int(stages), int(prefetch)), self._h)
+
+    def rowpass_layout(self):
+        """(wide, passes) of the row pass (kpm_rowpass_layout)."""
+        w, np_ = ctypes.c_int(), ctypes.c_int()
+        _check(self._lib().kpm_rowpass_layout(self._h, ctypes.byref(w), ctypes.byref(np_)), self._h)
+        return bool(w.value), np_.value
+
+    def set_rowpass_passes(self, passes: int):
+        """Wide row-pass layout with this many passes (0: automatic)."""
+        _check(self._lib().kpm_set_rowpass_passes(self._h, int(passes)), self._h)
 
     def test_rowpass_stall(self, on: bool = True):
         """Testing aid: the next tensor-core row pass stalls until its bounded waits

@@ -1173,6 +1173,26 @@ kpm_status kpm_set_rowpass(kpm_ctx* ctx, int stages, int prefetch) {
     return KPM_OK;
 }
 
+kpm_status kpm_set_rowpass_passes(kpm_ctx* ctx, int passes) {
+    if (!ctx) { g_err = "NULL context"; return KPM_EINVAL; }
+    if (!ctx->tc || passes < 0 || passes > 64) {
+        ctx->err = "row pass: a tensor-core context and 0..64 passes";
+        return KPM_EINVAL;
+    }
+    return guarded(ctx, [&] {
+        DeviceGuard g(ctx->device);
+        ctx->tc->set_layout(passes, ctx->st);
+        KPM_CUDA(cudaStreamSynchronize(ctx->st));
+    });
+}
+
+kpm_status kpm_rowpass_layout(const kpm_ctx* ctx, int* wide, int* passes) {
+    if (!ctx) { g_err = "NULL context"; return KPM_EINVAL; }
+    if (wide) *wide = ctx->tc ? (ctx->tc->wide ? 1 : 0) : 0;
+    if (passes) *passes = ctx->tc ? ctx->tc->npass : 0;
+    return KPM_OK;
+}
+
 kpm_status kpm_graphs_enable(kpm_ctx* ctx, int enable) {
     if (!ctx) { g_err = "NULL context"; return KPM_EINVAL; }
     ctx->graphs = enable != 0;

@@ -170,6 +170,13 @@ struct RowPass {
     int NS;                  // slots in use (n(n+1)/2); slots [NS, P) are padding
     int nst;                 // A stages in shared memory (2 or 3)
     int prefetch;            // L2 prefetch of the A rows this many tiles ahead (0: none)
+    // wide layout (more than 32736 column strings, or a row's sigma beyond shared
+    // memory): 16-bit targets without the sign (absent: 0xFFFF), the sign taken from
+    // the column string's occupations, and the targets split into npass ranges of
+    // span strings, one pass over the row's tiles per range
+    int npass;
+    int64_t span;
+    const uint32_t* cmask;   // [Nc] occupation masks of the column strings (wide layout)
     int* err;
     long long wait_cycles;   // limit of every mbarrier wait (clock64 cycles)
     int stall;               // test of the bounded waits: the MMA thread issues nothing, so
@@ -336,7 +343,7 @@ __device__ __forceinline__ bool wait_phase(uint64_t* mbar, uint32_t parity, vola
 // W[qq][s], formed in FP64 and split into NW pieces.  The block of W where both
 // excitations are diagonal ((pp|qq)) is zero in the image and in w_R: that part
 // of the diagonal of H is added exactly by the same-spin GEMM's epilogue.
-template <int P, bool FP16, int NW>
+template <int P, bool FP16, int NW, bool WIDE>
 __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
     constexpr int MAXF = P >= 32 ? P / 32 : 1;     // full chunks per scatter warp (upper bound)
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -347,9 +354,11 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
     uint8_t* sA = smem;                                               // [nst stages][2 pieces]
     uint8_t* sB = smem + 2 * nst * a_piece;                           // NW pieces of P x KR
     const uint32_t b_piece = (uint32_t)(P * KR * 2);
-    int* srow = reinterpret_cast<int*>(sB + NW * b_piece);            // Nc + RP_SINK, fixed point
+    // targets held per pass: all Nc, or a span of them (wide layout)
+    const int64_t Nrow = WIDE ? p.span : Nc;
+    int* srow = reinterpret_cast<int*>(sB + NW * b_piece);            // Nrow + RP_SINK, fixed point
     int64_t* rowoff = reinterpret_cast<int64_t*>(
-        (reinterpret_cast<uintptr_t>(srow + Nc + RP_SINK) + 15) & ~uintptr_t(15));  // [RP_MAXK]
+        (reinterpret_cast<uintptr_t>(srow + Nrow + RP_SINK) + 15) & ~uintptr_t(15));  // [RP_MAXK]
     uint16_t* rsl = reinterpret_cast<uint16_t*>(rowoff + RP_MAXK);    // [RP_MAXK]
     float* rmx = reinterpret_cast<float*>(
         (reinterpret_cast<uintptr_t>(rsl + RP_MAXK) + 15) & ~uintptr_t(15));  // [RP_MAXK]
@@ -357,7 +366,8 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
     unsigned* rred = reinterpret_cast<unsigned*>(rsc + 4);            // [2] row reductions
     double* wdg = reinterpret_cast<double*>(
         (reinterpret_cast<uintptr_t>(rred + 2) + 15) & ~uintptr_t(15));  // [P] w_R (FP64)
-    uintptr_t tail = (reinterpret_cast<uintptr_t>(wdg + P) + 15) & ~uintptr_t(15);
+    uint32_t* bm = reinterpret_cast<uint32_t*>(wdg + P);   // [P] orbitals strictly inside slot s
+    uintptr_t tail = (reinterpret_cast<uintptr_t>(bm + P) + 15) & ~uintptr_t(15);
     uint64_t* afree = reinterpret_cast<uint64_t*>(tail);   // [3] stage s free (MMA done)
     uint64_t* afull = afree + 3;                           // [3] stage s copied
     uint64_t* dfull = afree + 6;                           // [2] D buffer d written
@@ -379,6 +389,15 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
         }
         *abort_flag = 0;
         fence_mbar_init();
+    }
+    if (WIDE) {
+        // slot s = {a, b}, a < b: the sign of its excitation on a string is the parity
+        // of the string's occupations strictly between a and b (tables.cu)
+        for (int sl = tid; sl < P; sl += RP_THREADS) {
+            int a = 0, b = 0;
+            if (sl < p.NS) slot_pair(sl, a, b);
+            bm[sl] = (sl < p.NS && a < b) ? (((1u << b) - 1u) & ~((2u << a) - 1u)) : 0u;
+        }
     }
     if (warp == 0) {
         tmem_alloc(tmem_holder, p.ncols);
@@ -410,14 +429,17 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
     // and D buffer g & 1
     uint32_t g = 0;
 
-    for (int64_t idx = blockIdx.x; idx < nrows; idx += gridDim.x) {
-        const int64_t ir = idx;
+    // work items: (row, pass over a range of targets); one pass per row unless wide
+    const int npass = WIDE ? p.npass : 1;
+    for (int64_t idx = blockIdx.x; idx < nrows * npass; idx += gridDim.x) {
+        const int64_t ir = WIDE ? idx / npass : idx;
+        const int64_t lo = WIDE ? (idx - ir * npass) * Nrow : 0;   // first target of the pass
         // ---- row set-up: zero sigma; the row's source rows, slots and signs; B_R
         if (tid == 0) {
             rred[0] = 0u;
             rred[1] = 0u;
         }
-        for (int64_t j = tid; j < Nc + RP_SINK; j += RP_THREADS) srow[j] = 0;
+        for (int64_t j = tid; j < Nrow + RP_SINK; j += RP_THREADS) srow[j] = 0;
         for (int e = tid; e < RP_MAXK; e += RP_THREADS) {
             // off-diagonal entries, then the diagonal column (marker 0xFFFE), then padding
             if (e < p.rnexc) {
@@ -511,7 +533,8 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
             const int cw = warp - RP_SCATTER_WARPS;
             const int eo = lane & 7, g0 = lane >> 3;
             const int nu = KR / 4, kpg = KR / 8;
-            int32_t so[MAXU];                       // element offset in the piece, -1: padding
+            int64_t so[MAXU];                       // element offset in the piece, -1: padding
+                                                    // (beyond 2^31 at 18 orbitals)
 #pragma unroll
             for (int i = 0; i < MAXU; ++i) {
                 const int u = cw + RP_COPY_WARPS * i;
@@ -519,7 +542,7 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
                 if (u < nu) {
                     const int kc = u < kpg ? u : u - kpg;
                     const int64_t ro = rowoff[kc * 8 + eo];
-                    so[i] = ro >= 0 ? (int32_t)ro + 8 * g0 : -1;
+                    so[i] = ro >= 0 ? ro + 8 * g0 : -1;
                 }
             }
             auto copies = [&](int t, uint32_t stage) {
@@ -629,8 +652,11 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
             uint32_t w[MAXF][4], wt[3];
             // columns past Nc (the ragged last tile) sink every slot: cell Nc + lane
             // (the tile starts at a multiple of 128, so J mod 32 = lane)
-            const uint32_t sink = (uint32_t)Nc + (uint32_t)lane;
+            // (wide layout: absent slots and ragged columns read 0xFFFF, which no range
+            // holds, so they add into the sink cell Nrow + lane)
+            const uint32_t sink = WIDE ? 0xFFFFu : (uint32_t)Nc + (uint32_t)lane;
             const uint32_t sink2 = sink | (sink << 16);
+            uint32_t mj = 0, cmj = 0;     // wide layout: occupations of this column's string
             auto load_words = [&](int t) {
                 const int64_t jc = (int64_t)t * 128 + m;
                 const bool in = jc < Nc;
@@ -653,14 +679,26 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
                         wt[i] = in ? v : sink2;
                     }
                 }
+                if (WIDE) mj = __ldg(p.cmask + jcc);
             };
             // one slot: sigma[tgt] += sign * round(D), unconditionally (an absent
             // slot's target is this lane's sink cell)
-            auto add = [&](uint32_t word, int half, uint32_t dbits) {
-                const uint32_t tg = half ? (word >> 16) & 0x7FFFu : word & 0x7FFFu;
-                const uint32_t sg = half ? (word & 0x80000000u) : (word << 16) & 0x80000000u;
-                const int q = __float2int_rn(__uint_as_float(dbits ^ sg));
-                atomicAdd(srow + tg, q);
+            auto add = [&](uint32_t word, int half, int slot, uint32_t dbits) {
+                if (WIDE) {
+                    // target within this pass's range, else the lane's sink cell; sign
+                    // from the column string's occupations inside the slot
+                    const uint32_t t = half ? (word >> 16) : (word & 0xFFFFu);
+                    const uint32_t loc = t - (uint32_t)lo;
+                    const uint32_t tg = loc < (uint32_t)Nrow ? loc : (uint32_t)Nrow + (uint32_t)lane;
+                    const uint32_t sg = (uint32_t)(__popc(cmj & bm[slot]) & 1) << 31;
+                    const int q = __float2int_rn(__uint_as_float(dbits ^ sg));
+                    atomicAdd(srow + tg, q);
+                } else {
+                    const uint32_t tg = half ? (word >> 16) & 0x7FFFu : word & 0x7FFFu;
+                    const uint32_t sg = half ? (word & 0x80000000u) : (word << 16) & 0x80000000u;
+                    const int q = __float2int_rn(__uint_as_float(dbits ^ sg));
+                    atomicAdd(srow + tg, q);
+                }
             };
             bool ok = true;
             if (ntiles > 0) load_words(0);
@@ -700,19 +738,21 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
                     for (int i = 0; i < 4; ++i) cw[k][i] = w[k][i];
 #pragma unroll
                 for (int i = 0; i < 3; ++i) ct[i] = wt[i];
+                cmj = mj;
                 if (t + 1 < ntiles) load_words(t + 1);
 #pragma unroll
                 for (int k = 0; k < MAXF; ++k) {
                     if (k < nfull) {
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) add(cw[k][u >> 1], u & 1, dr[k][u]);
+                        for (int u = 0; u < 8; ++u)
+                            add(cw[k][u >> 1], u & 1, (wq + 4 * k) * 8 + u, dr[k][u]);
                     }
                 }
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
                     if (i < rem) {
-                        add(ct[i], 0, dt[2 * i]);
-                        add(ct[i], 1, dt[2 * i + 1]);
+                        add(ct[i], 0, tail0 + 2 * i, dt[2 * i]);
+                        add(ct[i], 1, tail0 + 2 * i + 1, dt[2 * i + 1]);
                     }
                 }
             }
@@ -720,7 +760,11 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
         g += (uint32_t)ntiles;
         __syncthreads();
         if (*abort_flag) break;
-        for (int64_t j = tid; j < Nc; j += RP_THREADS) p.Y[ir * Nc + j] = (float)srow[j] * rsc[2];
+        {
+            const int64_t nout = Nc - lo < Nrow ? Nc - lo : Nrow;   // this pass's targets
+            for (int64_t j = tid; j < nout; j += RP_THREADS)
+                p.Y[ir * Nc + lo + j] = (float)srow[j] * rsc[2];
+        }
         __syncthreads();
     }
     tc_fence_before();
@@ -793,15 +837,16 @@ __global__ void k_wimg(const double* __restrict__ eri, int n, int P, int NS, int
 // tgt | (sgn < 0) << 15; slots without an entry hold the sink ns + (j mod 32).
 // Stored per chunk of 8 slots: the 128-bit word (s/8, j) holds slots
 // 8*(s/8) .. 8*(s/8)+7, slot s in 16-bit half s%8.
-__global__ void k_slot_fill(uint16_t* __restrict__ tslot, int64_t count, int64_t ns) {
+// Wide layout (wide != 0): a slot holds the target alone, 0xFFFF when absent.
+__global__ void k_slot_fill(uint16_t* __restrict__ tslot, int64_t count, int64_t ns, int wide) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
          i += (int64_t)gridDim.x * blockDim.x)
-        tslot[i] = (uint16_t)(ns + ((i >> 3) % ns & 31));
+        tslot[i] = wide ? (uint16_t)0xFFFFu : (uint16_t)(ns + ((i >> 3) % ns & 31));
 }
 
 __global__ void k_slot_table(const int32_t* __restrict__ tgt, const uint16_t* __restrict__ pq,
                              const int8_t* __restrict__ sgn, int64_t ns, int nexc, int n,
-                             uint16_t* __restrict__ tslot) {
+                             uint16_t* __restrict__ tslot, int wide) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ns * nexc) return;
     const int64_t j = i / nexc;
@@ -809,7 +854,7 @@ __global__ void k_slot_table(const int32_t* __restrict__ tgt, const uint16_t* __
     if (a > b) { int t = a; a = b; b = t; }
     const int s = b * (b + 1) / 2 + a;
     tslot[((int64_t)(s >> 3) * ns + j) * 8 + (s & 7)] =
-        (uint16_t)(tgt[i] | (sgn[i] < 0 ? 0x8000 : 0));
+        wide ? (uint16_t)tgt[i] : (uint16_t)(tgt[i] | (sgn[i] < 0 ? 0x8000 : 0));
 }
 
 // row-string tables of the off-diagonal entries (p != q), in table order: target
@@ -868,9 +913,11 @@ uint32_t tmem_cols(int P) {
     return c;
 }
 
-size_t rowpass_smem(int P, int NW, int KR, int64_t Nc, int nst) {
-    return (size_t)2 * nst * KR * 256 + (size_t)2 * NW * P * KR + 4 * (size_t)(Nc + RP_SINK) + 16 +
-           10 * RP_MAXK + 16 + 4 * RP_MAXK + 24 + 16 + 8 * (size_t)P + 16 + 10 * 8 + 16;
+// Nrow: targets held in shared memory (all column strings, or one pass's span)
+size_t rowpass_smem(int P, int NW, int KR, int64_t Nrow, int nst) {
+    return (size_t)2 * nst * KR * 256 + (size_t)2 * NW * P * KR + 4 * (size_t)(Nrow + RP_SINK) +
+           16 + 10 * RP_MAXK + 16 + 4 * RP_MAXK + 24 + 16 + 8 * (size_t)P + 4 * (size_t)P + 16 +
+           10 * 8 + 16;
 }
 
 // W in RP_NW 16-bit pieces (2: ~2^-22 relative per (pq|rs); 3: ~2^-33, a fourth
@@ -880,10 +927,25 @@ constexpr int RP_NW = 2;
 
 template <int P>
 void* rowpass_fn(bool fp16) {
-    return fp16 ? (void*)k_rowpass<P, true, RP_NW> : (void*)k_rowpass<P, false, RP_NW>;
+    return fp16 ? (void*)k_rowpass<P, true, RP_NW, false> : (void*)k_rowpass<P, false, RP_NW, false>;
+}
+template <int P>
+void* rowpass_fn_wide(bool fp16) {
+    return fp16 ? (void*)k_rowpass<P, true, RP_NW, true> : (void*)k_rowpass<P, false, RP_NW, true>;
 }
 
-void* rowpass_kernel(int P, bool fp16) {
+// The wide layout is instantiated for 17 and 18 orbitals (P = 160, 176), which
+// need it, and for 12 orbitals (P = 80), where the tests compare it with the
+// plain layout.
+void* rowpass_kernel(int P, bool fp16, bool wide) {
+    if (wide) {
+        switch (P) {
+            case 80: return rowpass_fn_wide<80>(fp16);
+            case 160: return rowpass_fn_wide<160>(fp16);
+            case 176: return rowpass_fn_wide<176>(fp16);
+            default: return nullptr;
+        }
+    }
     switch (P) {
         case 16: return rowpass_fn<16>(fp16);
         case 32: return rowpass_fn<32>(fp16);
@@ -901,7 +963,7 @@ void* rowpass_kernel(int P, bool fp16) {
 }  // namespace
 
 size_t rowpass_smem_bytes(const TcSigma& t, int stages) {
-    return rowpass_smem(t.P, t.nw, t.KR, t.nsa > t.nsb ? t.nsa : t.nsb, stages);
+    return rowpass_smem(t.P, t.nw, t.KR, t.wide ? t.span : t.nsb, stages);
 }
 
 void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
@@ -917,7 +979,6 @@ void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
     dim = nsa * nsb;
     fp16 = use_fp16;
     nw = RP_NW;
-    kernel = rowpass_kernel(P, fp16);
     // off-diagonal entries of a row string, m (n - m), and one column for its m
     // diagonal entries; at least one K step, so that a row without any (no alpha
     // electrons) multiplies padding (B_R = 0) and D is exactly zero instead of
@@ -925,9 +986,8 @@ void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
     noff = A.m * (n - A.m);
     ndiag = A.m > 0 ? 1 : 0;
     KR = noff + ndiag > 0 ? ((noff + ndiag + 15) / 16) * 16 : 16;
-    // 15-bit targets: every string index and sink cell (ns + 31) below 2^15
-    if (!kernel || KR > RP_MAXK || A.ns > 32768 - RP_SINK || B.ns > 32768 - RP_SINK)
-        KPM_THROW(KPM_EUNSUPPORTED, "tensor-core sigma supports up to 16 orbitals");
+    if (KR > RP_MAXK || B.ns > 65536 - 2 * RP_SINK)
+        KPM_THROW(KPM_EUNSUPPORTED, "tensor-core sigma supports up to 18 orbitals");
     int dev = 0;
     KPM_CUDA(cudaGetDevice(&dev));
     cudaDeviceProp prop;
@@ -935,23 +995,7 @@ void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
     if (prop.major != 10)
         KPM_THROW(KPM_EUNSUPPORTED, "tensor-core sigma needs a Blackwell (sm_10x) GPU");
     nsm = prop.multiProcessorCount;
-    int64_t ncmax = nsa > nsb ? nsa : nsb;
-    // three A stages where they fit (the copies of a tile then have two MMA
-    // durations to land), else two
-    nst = 3;
-    smem_bytes = rowpass_smem(P, nw, KR, ncmax, nst);
-    if (smem_bytes > (size_t)prop.sharedMemPerBlockOptin) {
-        nst = 2;
-        smem_bytes = rowpass_smem(P, nw, KR, ncmax, nst);
-    }
-    // at least ~116 KB so that exactly one CTA (and one TMEM allocation) fits per SM
-    size_t floor_bytes = 116 * 1024;
-    if (smem_bytes < floor_bytes) smem_bytes = floor_bytes;
-    if (smem_bytes > (size_t)prop.sharedMemPerBlockOptin)
-        KPM_THROW(KPM_EUNSUPPORTED, "tensor-core sigma: rows of %lld strings need %zu B of shared memory",
-                  (long long)ncmax, smem_bytes);
-    KPM_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem_bytes));
+    smem_optin = prop.sharedMemPerBlockOptin;
     // W scaled by a power of two so that |W| < 2^14 (FP16 range); BF16 needs none
     wscale = 1.0f;
     if (fp16 && wmax > 0.0) {
@@ -970,20 +1014,9 @@ void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
                                                            wimg.as<uint16_t>(), (double)wscale);
     KPM_LAUNCHED();
 
-    auto build_slots = [&](const SpinTables& T, DevBuf& out) {
-        size_t count = (size_t)P * T.ns;
-        out.alloc(count * sizeof(uint16_t));
-        k_slot_fill<<<1024, 256, 0, st>>>(out.as<uint16_t>(), (int64_t)count, T.ns);
-        KPM_LAUNCHED();
-        int64_t ne = T.ns * T.nexc;
-        if (ne > 0) {
-            k_slot_table<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
-                T.tgt.as<int32_t>(), T.pq.as<uint16_t>(), T.sgn.as<int8_t>(), T.ns, T.nexc, n,
-                out.as<uint16_t>());
-            KPM_LAUNCHED();
-        }
-    };
-    build_slots(B, slot_b);
+    // the plain layout where its 15-bit targets and one row's sigma fit (three A
+    // stages, else two), else the wide one with as few passes as fit
+    set_layout(0, st);
     {
         const int64_t no = A.ns * (int64_t)noff;
         rslot_a.alloc((size_t)(no > 0 ? no : 1) * sizeof(uint16_t));
@@ -1004,7 +1037,63 @@ void TcSigma::init(const SpinTables& A, const SpinTables& B, const double* d_h1,
     dense.init(A, B, &A == &B, err.as<int>(), st);
     dense.diag_full = d_diag;
     dense.autotune(st);
-    autotune(st);
+    if (!wide) autotune(st);
+}
+
+// Chooses the row pass's layout (passes = 0: automatic; >= 1: the wide layout
+// with that many passes, where it is instantiated), sizes its shared memory and
+// builds the column strings' slot table in the matching format.
+void TcSigma::set_layout(int passes, cudaStream_t st) {
+    const size_t optin = smem_optin;
+    bool w = passes > 0;
+    int np = passes > 0 ? passes : 1;
+    int stg = 3;
+    if (!w) {
+        const bool fits15 = nsb <= 32768 - RP_SINK && rowpass_kernel(P, fp16, false);
+        if (fits15 && rowpass_smem(P, nw, KR, nsb, 3) <= optin) stg = 3;
+        else if (fits15 && rowpass_smem(P, nw, KR, nsb, 2) <= optin) stg = 2;
+        else w = true;   // (also where only the wide kernel exists for P: 17, 18 orbitals)
+    }
+    int64_t sp = nsb;
+    if (w) {
+        stg = 2;
+        if (passes <= 0)
+            while (rowpass_smem(P, nw, KR, (nsb + np - 1) / np, 2) > optin && np < 64) ++np;
+        sp = (nsb + np - 1) / np;
+        if (sp < 1) sp = 1;
+    }
+    void* kfn = rowpass_kernel(P, fp16, w);
+    if (!kfn)
+        KPM_THROW(w ? KPM_EINVAL : KPM_EUNSUPPORTED,
+                  "tensor-core sigma: no row-pass kernel for %d slots in the %s layout", P,
+                  w ? "wide" : "plain");
+    size_t sm = rowpass_smem(P, nw, KR, sp, stg);
+    // at least ~116 KB so that exactly one CTA (and one TMEM allocation) fits per SM
+    const size_t floor_bytes = 116 * 1024;
+    if (sm < floor_bytes) sm = floor_bytes;
+    if (sm > optin)
+        KPM_THROW(KPM_EUNSUPPORTED, "tensor-core sigma: %lld targets per pass need %zu B of shared memory",
+                  (long long)sp, sm);
+    KPM_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const size_t count = (size_t)P * tb->ns;
+    if (!slot_b.p || w != wide) {
+        slot_b.alloc(count * sizeof(uint16_t));
+        k_slot_fill<<<1024, 256, 0, st>>>(slot_b.as<uint16_t>(), (int64_t)count, tb->ns, w ? 1 : 0);
+        KPM_LAUNCHED();
+        const int64_t ne = tb->ns * tb->nexc;
+        if (ne > 0) {
+            k_slot_table<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(
+                tb->tgt.as<int32_t>(), tb->pq.as<uint16_t>(), tb->sgn.as<int8_t>(), tb->ns,
+                tb->nexc, n, slot_b.as<uint16_t>(), w ? 1 : 0);
+            KPM_LAUNCHED();
+        }
+    }
+    kernel = kfn;
+    wide = w;
+    npass = np;
+    span = sp;
+    nst = stg;
+    smem_bytes = sm;
 }
 
 void TcSigma::apply(const float* x, float* y, int ncol, cudaStream_t st) {
@@ -1051,10 +1140,11 @@ void TcSigma::launch_rowpass(const uint16_t* xh, const uint16_t* xl, float* Y, i
                rtgt_a.as<int32_t>(), rslot_a.as<uint16_t>(), noff, ndiag, KR,
                ta->masks.as<uint32_t>(), wdiag.as<double>(),
                wimg.as<uint16_t>(), nc, am, rowmax.as<float>(), wscale, tb->nexc, NS, stages,
-               prefetch, err.as<int>(), stall_next ? STALL_WAIT_CYCLES : WAIT_CYCLES,
-               stall_next ? 1 : 0};
+               prefetch, npass, span, tb->masks.as<uint32_t>(), err.as<int>(),
+               stall_next ? STALL_WAIT_CYCLES : WAIT_CYCLES, stall_next ? 1 : 0};
     stall_next = false;
-    int g1 = (int)(nsa < nsm ? nsa : nsm);
+    const int64_t items = nsa * (int64_t)npass;
+    int g1 = (int)(items < nsm ? items : nsm);
     void* args1[] = {&p1};
     if (prof) {
         if ((int)ev.size() < ev_used + 2) {

@@ -35,6 +35,12 @@ struct TcSigma {
     int nst = 2;                  // A stages of the row pass (at most 3, where shared memory
                                   // allows; autotuned)
     int rp_prefetch = 4;          // L2 prefetch distance of the row pass, tiles (autotuned)
+    // row-pass layout: plain (15-bit targets with the sign, one pass) or wide (16-bit
+    // targets, sign from the column string, targets split into npass ranges of span)
+    bool wide = false;
+    int npass = 1;
+    int64_t span = 0;
+    size_t smem_optin = 0;
     bool stall_next = false;      // test of the bounded waits: the next row pass stalls (see
                                   // kpm_test_rowpass_stall)
     size_t smem_bytes = 0;
@@ -52,6 +58,9 @@ struct TcSigma {
                         int prefetch, cudaStream_t st);
     // Times the row pass's stages x prefetch candidates once per device and shape.
     void autotune(cudaStream_t st);
+    // Row-pass layout: passes = 0 automatic, >= 1 the wide layout with that many
+    // passes (KPM_EINVAL where no wide kernel is instantiated for P).
+    void set_layout(int passes, cudaStream_t st);
     // Reads and clears the device error flag (synchronises the stream).
     int check(cudaStream_t st);
 

@@ -721,6 +721,64 @@ def test_sigma_18_orbitals_sampled_rows(torch):
     k.close()
 
 
+@pytest.mark.parametrize("prec", MIXED)
+def test_rowpass_wide_layout_equals_plain_12o(torch, prec):
+    """The wide row-pass layout (16-bit targets, sign from the column string's
+    occupations, targets split over passes) gives the plain layout's sigma bit
+    for bit at 12 orbitals, with one pass and with three; sizes without a wide
+    kernel refuse it."""
+    from paper_2506_07430_gb300 import KPMError
+    I = synthetic.integrals(12, 6, 6, 2506072)
+    k = _kpm(I, 12, 6, 6, prec)
+    assert k.rowpass_layout() == (False, 1)
+    x = torch.from_numpy(synthetic.random_state(k.dim, 13)).float().cuda()
+    y0 = k.sigma(x).clone()
+    for passes in (1, 3):
+        k.set_rowpass_passes(passes)
+        assert k.rowpass_layout() == (True, passes)
+        y = k.sigma(x)
+        k.synchronize()
+        assert torch.equal(y, y0), passes
+    k.set_rowpass_passes(0)
+    assert k.rowpass_layout() == (False, 1)
+    assert torch.equal(k.sigma(x), y0)
+    k.close()
+    I = synthetic.integrals(10, 5, 5, 2506071)
+    k = _kpm(I, 10, 5, 5, prec)
+    with pytest.raises(KPMError):
+        k.set_rowpass_passes(2)
+    k.close()
+
+
+def test_sigma_mixed_18_orbitals_sampled_rows(torch):
+    """18 orbitals, 9+9 electrons on the tensor cores (48,620 strings per spin: the
+    wide row-pass layout in several passes; dense same-spin GEMMs of 48,620^2):
+    sigma on sampled rows vs the oracle's Slater-Condon row-pull."""
+    from oracle.hamiltonian import hash_vector
+    n, m = 18, 9
+    I = synthetic.integrals(n, m, m, seed=2506075)
+    k = _kpm(I, n, m, m, "mixed")
+    wide, passes = k.rowpass_layout()
+    assert wide and passes >= 2
+    dim = k.dim
+    x = _hash_vector_dev(torch, dim)
+    probe = np.array([0, 1, 2**31 + 5, dim - 1])
+    assert np.array_equal(x[torch.tensor(probe, device="cuda")].cpu().numpy().astype(np.float64),
+                          hash_vector(probe))
+    y = k.sigma(x)
+    k.synchronize()
+    del x
+    sc = oracle.SlaterCondon(I.h1, I.eri, n, m, m)
+    rng = np.random.default_rng(18)
+    rows = np.concatenate([rng.choice(dim, 3000, replace=False), [0, dim - 1, 2**31 + 5]])
+    ref = sc.sigma_rows_hash(rows)
+    got = y[torch.tensor(rows, device="cuda")].cpu().numpy().astype(np.float64)
+    err = np.abs(got - ref).max() / np.abs(ref).max()
+    print("18o mixed sampled sigma error / max|y|:", err)
+    assert err < MIXED_TOL["mixed"]
+    k.close()
+
+
 @pytest.mark.parametrize("prec,n,ne", [("fp64", 8, 4), ("fp32", 10, 5), ("mixed", 10, 5)])
 def test_graph_steps_equal_direct_steps(torch, prec, n, ne):
     """Recursion steps replayed from captured CUDA graphs give the same moments,
