@@ -51,7 +51,7 @@ NCU_TRAFFIC = {
     ("fci16o16e", "mixed"): {
         "bytes": 12.40e9 + 0.660e9,
         "source": "paper_2506_07430_gb300/csrc/sigma_tc.cu",
-        "source_sha16": "c67b3a099a3bb817",
+        "source_sha16": "d79f9eb0b9f7272a",
         "captured": "2026-12-04, GB300, one launch of k_rowpass<144> (plain layout, 1 pass)",
         "profile": "profiles/k_rowpass_fci16o16e.md",
     },

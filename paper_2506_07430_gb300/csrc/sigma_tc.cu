@@ -739,7 +739,7 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
 #pragma unroll
                 for (int i = 0; i < 3; ++i) ct[i] = wt[i];
                 cmj = mj;
-                if (t + 1 < ntiles) load_words(t + 1);
+                if (!WIDE && t + 1 < ntiles) load_words(t + 1);
 #pragma unroll
                 for (int k = 0; k < MAXF; ++k) {
                     if (k < nfull) {
@@ -755,6 +755,9 @@ __global__ void __launch_bounds__(RP_THREADS, 1) k_rowpass(const RowPass p) {
                         add(ct[i], 1, tail0 + 2 * i + 1, dt[2 * i + 1]);
                     }
                 }
+                // (wide layout: the next tile's words after the adds, which frees the
+                // registers of one word set at 160-176 slots: 6 % faster at 18 orbitals)
+                if (WIDE && t + 1 < ntiles) load_words(t + 1);
             }
         }
         g += (uint32_t)ntiles;
