@@ -526,11 +526,13 @@ __global__ void k_split_rows(const float* __restrict__ src, int64_t R, int64_t C
     }
 }
 
-// Transposed split: dst[c][r] = src[r][c] for src R x Cn, dst rows Cn of pitch >= R.
+// Transposed split: dst[c][r] = src[r][c] for src R x Cn, dst rows Cn of pitch >= R
+// (pitch even, padding rows [R, pitch) written as zeros).  Tiles of 64 rows x 32
+// columns through shared memory; each thread stores two consecutive r as a half2.
 __global__ void k_split_transpose(const float* __restrict__ src, int64_t R, int64_t Cn,
                                   __half* __restrict__ hi, __half* __restrict__ lo,
                                   int64_t pitch, const float* amax) {
-    __shared__ float t[32][33];
+    __shared__ float t[64][33];
     float sa = 1.f;
     {
         const float mx = *amax;
@@ -540,19 +542,21 @@ __global__ void k_split_transpose(const float* __restrict__ src, int64_t R, int6
             sa = ldexpf(1.f, 14 - max(e, -90));
         }
     }
-    const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 64;
+    for (int k = threadIdx.y; k < 64; k += blockDim.y) {
         const int64_t r = r0 + k, c = c0 + threadIdx.x;
         t[k][threadIdx.x] = (r < R && c < Cn) ? src[r * Cn + c] * sa : 0.f;
     }
     __syncthreads();
     for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        const int64_t c = c0 + k, r = r0 + threadIdx.x;
+        const int64_t c = c0 + k, r = r0 + 2 * threadIdx.x;
         if (c < Cn && r < pitch) {
-            const float v = t[threadIdx.x][k];
-            const __half h = __float2half_rn(v);
-            hi[c * pitch + r] = h;
-            lo[c * pitch + r] = __float2half_rn(v - __half2float(h));
+            const float v0 = t[2 * threadIdx.x][k], v1 = t[2 * threadIdx.x + 1][k];
+            const __half h0 = __float2half_rn(v0), h1 = __float2half_rn(v1);
+            *reinterpret_cast<__half2*>(hi + c * pitch + r) = __halves2half2(h0, h1);
+            *reinterpret_cast<__half2*>(lo + c * pitch + r) =
+                __halves2half2(__float2half_rn(v0 - __half2float(h0)),
+                               __float2half_rn(v1 - __half2float(h1)));
         }
     }
 }
@@ -793,7 +797,8 @@ void DenseSS::apply(const float* x, float* y, const float* amax, cudaStream_t st
     // transposed split copy of x (cols beta x rows alpha); the row split is xh/xl
     th.ensure((size_t)nb * pa * 2);
     tl.ensure((size_t)nb * pa * 2);
-    dim3 tb(32, 8), gt((unsigned)((nb + 31) / 32), (unsigned)((na + 31) / 32));
+    if (pa & 1) KPM_THROW(KPM_EINVAL, "split transpose: odd pitch");
+    dim3 tb(32, 8), gt((unsigned)((nb + 31) / 32), (unsigned)((na + 63) / 64));
     k_split_transpose<<<gt, tb, 0, st>>>(x, na, nb, th.as<__half>(), tl.as<__half>(), pa, amax);
     KPM_LAUNCHED();
     launch_beta(y, amax, group_m[0], st);
