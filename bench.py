@@ -92,8 +92,9 @@ def parse_args():
     p.add_argument("--gs-cycles", type=int, default=3, help="ground-state restart cycles")
     p.add_argument("--gs-tol", type=float, default=1e-4, help="ground-state residual target")
     p.add_argument("--e2e-requests", type=int, default=1)
-    p.add_argument("--e2e-moments", type=int, default=256,
-                   help="moments per end-to-end request (kpm_moments_host)")
+    p.add_argument("--e2e-moments", type=int, default=None,
+                   help="moments per end-to-end request (kpm_moments_host); default: the "
+                        "workload's own (2048 at 16 orbitals)")
     p.add_argument("--check-steps", type=int, default=12,
                    help="Chebyshev steps of the same recursion run on the FP64 path (untimed) "
                         "to report the per-moment error of the timed precision")
@@ -420,7 +421,8 @@ def run_ours(args, ws, rank, local, pg):
     pinned = torch.empty(dim, dtype=torch.float64, pin_memory=True)
     pinned.copy_(torch.from_numpy(psi0_host))
     pin_np = pinned.numpy()
-    nm_e2e = max(4, 2 * (args.e2e_moments // 2))
+    nm_e2e = args.e2e_moments if args.e2e_moments is not None else w["nmoments"]
+    nm_e2e = max(4, 2 * (nm_e2e // 2))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.e2e_requests):
