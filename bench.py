@@ -264,9 +264,10 @@ def same_spin_neighbours(n, m):
 _ORACLE_CACHE = {}
 
 
-def oracle_rate(w, seconds: float, seed: int = 4):
+def oracle_rate(w, seconds: float, seed: int = 4, threads: int = 0):
     """Chebyshev steps/s of the CPU oracle, extrapolated from a timed sample of
-    Slater-Condon row-pull rows plus the FP64 update of the same rows."""
+    Slater-Condon row-pull rows plus the FP64 update of the same rows; on all host
+    cores (threads = 0) or on `threads` of them."""
     import oracle
     key = (w["norb"], w["nalpha"], w["nbeta"], w["seed"])
     if key not in _ORACLE_CACHE:
@@ -275,6 +276,18 @@ def oracle_rate(w, seconds: float, seed: int = 4):
         x = np.random.default_rng(seed).standard_normal(sc.dim)
         _ORACLE_CACHE[key] = (sc, x)
     sc, x = _ORACLE_CACHE[key]
+    full = oracle.hamiltonian.omp_threads()
+    if threads:
+        oracle.hamiltonian.set_omp_threads(threads)
+    try:
+        return _oracle_rate_timed(sc, x, seconds, seed)
+    finally:
+        if threads:
+            oracle.hamiltonian.set_omp_threads(full)
+
+
+def _oracle_rate_timed(sc, x, seconds, seed):
+    import oracle
     rng = np.random.default_rng(seed + 1)
     rows = rng.choice(sc.dim, 2000, replace=False)
     t0 = time.perf_counter()
@@ -435,6 +448,9 @@ def run_ours(args, ws, rank, local, pg):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, meta = oracle_rate(w, args.cpu_seconds)
         cpu = dict(value=v, unit=UNIT, **meta)
+        # the same oracle on one core (a third of the time budget)
+        v1, meta1 = oracle_rate(w, args.cpu_seconds / 3, threads=1)
+        cpu["one_core"] = {"value": v1, "cores": meta1["cores"], "sample": meta1["sample"]}
 
     out = {
         "metric": metric_for(w), "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": steps,

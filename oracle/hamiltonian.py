@@ -72,6 +72,8 @@ def _lib():
             lib.sc_dipole_rows.restype = None
             lib.sc_dipole_rows.argtypes = [P, P, P, I64, P, P]
             lib.sc_omp_threads.restype = ctypes.c_int
+            lib.sc_set_threads.restype = None
+            lib.sc_set_threads.argtypes = [ctypes.c_int]
             lib.sc_sigma_rows_hash.restype = None
             lib.sc_sigma_rows_hash.argtypes = [P, P, I64, P]
             lib.sc_hashvec.restype = ctypes.c_double
@@ -82,6 +84,11 @@ def _lib():
 
 def omp_threads() -> int:
     return int(_lib().sc_omp_threads())
+
+
+def set_omp_threads(n: int) -> None:
+    """Threads of the later oracle calls (timing on one core or on all)."""
+    _lib().sc_set_threads(int(n))
 
 
 class _CSys(ctypes.Structure):

@@ -301,3 +301,14 @@ int sc_omp_threads(void) {
     return 1;
 #endif
 }
+
+/* Sets the number of OpenMP threads of the later calls (n >= 1; a no-op without
+   OpenMP): lets a caller time the oracle on one core as well as on all. */
+void sc_set_threads(int n) {
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
